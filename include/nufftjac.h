@@ -1,0 +1,148 @@
+/*
+ * nufftjac.h -- C ABI of the GB300 (sm_103a) NUFFT / NUFFT-Jacobian library.
+ *
+ * Operations (Wang & Fessler, "Efficient approximation of Jacobian matrices
+ * involving a non-uniform fast Fourier transform"):
+ *   forward  y = A(omega) x, A_ij = exp(-i omega_i . r_j)       Sec. II-B, Eq. (e,ndft)
+ *            approximated by a NUFFT: scaling s_n, zero-padded K-point FFT,
+ *            J-tap interpolation                                  Appendix (NUFFT entries)
+ *   adjoint  x = A' y                                             Sec. II-D
+ *   sensitivity maps E = (I kron A) S, S_c = diag(s_c)            Sec. II-G
+ *   d(Ax)/d omega^[d] = -i diag{A (x . r^[d])}                    Sec. II-C, Eq. (e,Ax)
+ *   VJP  dL/d omega = Re{(-i A(x . r^[d]))' . v}                  Sec. III, Eq. (e,jac,Ax,v)
+ *   d(A'y)/d omega^[d] = i diag{r^[d]} A' diag{y}                 Sec. II-D, Eq. (e,A'y)
+ *
+ * Conventions shared by every entry point
+ *   - Every array argument is DEVICE memory owned by the caller, contiguous,
+ *     and must stay valid until the work queued on `stream` has finished.
+ *     Complex arrays are interleaved float pairs (re, im), 8-byte aligned.
+ *   - Images are C-ordered (N_1, ..., N_D), last axis fastest.  Voxel centre
+ *     r_j^[d] = n_d - N_d/2 (integer voxel units; every N_d must be even).
+ *   - omega is float32 [D][M] (row d holds omega^[d]) in radians per voxel;
+ *     any value is accepted (A is 2*pi-periodic in omega because r is integer).
+ *   - k-space arrays (y, v, dy) are [C][M] in the caller's point order.
+ *   - smaps == NULL: x is [C][N] (one image per channel) and the adjoint
+ *     returns [C][N].  smaps != NULL: smaps is [C][N], x is [N], and the
+ *     adjoint returns sum_c conj(s_c) A' y_c, shape [N].
+ *   - Gradients follow the real-valued convention: for a real loss L and
+ *     k-space output y, v = dL/dRe(y) + i dL/dIm(y); grad_x is returned in the
+ *     same convention and grad_omega = dL/d omega exactly (no factor 2).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All calls
+ *     are asynchronous and stream-ordered; none synchronises the host except
+ *     nufft_plan / nufft_set_points when the point capacity must grow.
+ *   - Return NUFFT_OK (0) or a negative status.  Nothing is thrown across the
+ *     ABI.  An asynchronous kernel fault is reported by a later call.
+ *     nufft_last_error() gives a readable message for the calling thread.
+ *   - A plan is not thread-safe; distinct plans are independent.
+ */
+#ifndef NUFFTJAC_H
+#define NUFFTJAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nufft_plan_s* nufft_plan_t;
+
+typedef struct {
+    float re, im;
+} nufft_cfloat;
+
+enum {
+    NUFFT_OK = 0,
+    NUFFT_ERR_INVALID_ARG = -1, /* null pointer, bad size, C out of range */
+    NUFFT_ERR_UNSUPPORTED = -2, /* D not in {1,2,3}, odd N_d, J out of [2,8], grid too large */
+    NUFFT_ERR_OOM = -3,         /* device allocation failed */
+    NUFFT_ERR_CUDA = -4,        /* a CUDA runtime call or kernel launch failed */
+    NUFFT_ERR_TIMEOUT = -5      /* reserved: a bounded device wait gave up */
+};
+
+/* Plan options.  Fields left 0 take the defaults noted. */
+typedef struct {
+    int dim;          /* D, 1..3 */
+    int64_t n[3];     /* image size N_d (even), d < dim */
+    double sigma;     /* oversampling factor, > 1 (0 -> 2.0); K_d = smallest even
+                         2,3,5-smooth integer >= sigma N_d, K_d <= 4096 */
+    int J;            /* interpolation width, 2..8 (0 -> 6) */
+    double beta;      /* Kaiser-Bessel shape (<= 0 -> Beatty et al.:
+                         pi sqrt((J/sigma)^2 (sigma-1/2)^2 - 0.8)) */
+    int max_coils;    /* largest C any call on this plan will pass, 1..128 (0 -> 1) */
+    int bin_size[3];  /* spread tile edge per dim (0 -> automatic) */
+    int reserved[4];
+} nufft_opts;
+
+/* Fill *o with defaults for a D-dimensional image of size n[0..D-1]. */
+void nufft_default_opts(nufft_opts* o, int dim, const int64_t* n);
+
+/* Create a plan: tables, workspace for max_coils channels, and the bin sort of
+ * the m points in omega (Appendix: offsets k_m and coefficients u_j(omega_m)
+ * depend on omega only).  m may be 0.  *out receives the plan. */
+int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* omega, void* stream);
+
+/* Re-sort after omega changed (every trajectory update).  m may differ from
+ * the plan's current m; growing past the capacity reallocates (synchronising). */
+int nufft_set_points(nufft_plan_t p, int64_t m, const float* omega, void* stream);
+
+/* y[C][M] = E x: forward NUFFT of each coil image (Sec. II-B, II-G). */
+int nufft_forward(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cfloat* smaps,
+                  nufft_cfloat* y, void* stream);
+
+/* x = E' y: adjoint NUFFT (Sec. II-D), summed over coils when smaps != NULL. */
+int nufft_adjoint(nufft_plan_t p, int C, const nufft_cfloat* y, const nufft_cfloat* smaps,
+                  nufft_cfloat* x, void* stream);
+
+/* Forward-mode product (Eq. (e,Ax)): dy_c = sum_d domega^[d] . (-i) A(s_c . x . r^[d]).
+ * domega is float [D][M].  If y_or_null != NULL, y = E x comes out of the same
+ * interpolation launch (1+D channels per coil share the kernel weights). */
+int nufft_jvp_omega(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cfloat* smaps,
+                    const float* domega, nufft_cfloat* dy, nufft_cfloat* y_or_null, void* stream);
+
+/* Reverse-mode products for incoming gradient v [C][M] (Eq. (e,jac,Ax,v)):
+ *   grad_omega[d][i] = sum_c Re{ conj(v_ci) (-i) [A(s_c . x . r^[d])]_i }   (float [D][M])
+ *   grad_x = E' v                                                          (as nufft_adjoint)
+ * Either output may be NULL to skip it.  The adjoint operator's omega-VJP
+ * (Eq. (e,A'y)) is this call with (x, v) <- (incoming image gradient, y). */
+int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cfloat* smaps,
+                      const nufft_cfloat* v, float* grad_omega, nufft_cfloat* grad_x, void* stream);
+
+/* Device bytes a plan with these options and m points would allocate. */
+size_t nufft_workspace_bytes(const nufft_opts* o, int64_t m);
+
+/* Plan facts for callers and benchmarks. */
+typedef struct {
+    int dim;
+    int64_t n[3], k[3];      /* image and oversampled grid sizes */
+    int J;
+    double sigma, beta;
+    int64_t m;               /* current number of points */
+    int bin_size[3], nbins;  /* spread tiles */
+    int max_coils;
+    size_t workspace_bytes;  /* device bytes held by the plan */
+} nufft_plan_info;
+int nufft_get_info(nufft_plan_t p, nufft_plan_info* info);
+
+/* Free the plan and its device memory (synchronises the plan's last stream). */
+void nufft_destroy(nufft_plan_t p);
+
+const char* nufft_status_string(int status);
+const char* nufft_last_error(void);
+
+/* ---- measurement hooks -------------------------------------------------
+ * Kernel launches made by this library in this process (all plans). */
+int64_t nufft_launch_count(void);
+
+/* When enabled, every kernel the plan launches is bracketed by CUDA events on
+ * the launching stream.  nufft_profile_read synchronises those events and
+ * returns, per kernel kind, the launch count and summed milliseconds, then
+ * clears them.  names[i] points to static strings. */
+int nufft_profile_enable(nufft_plan_t p, int enable);
+int nufft_profile_read(nufft_plan_t p, int max_kinds, const char** names, int* launches,
+                       double* total_ms, int* n_kinds);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NUFFTJAC_H */

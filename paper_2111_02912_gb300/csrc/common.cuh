@@ -1,0 +1,71 @@
+// Shared types and device helpers of the NUFFT-Jacobian kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nj {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxStages = 12;
+constexpr int kKbTerms = 32;   // Horner terms of the Kaiser-Bessel power series
+constexpr int kJMax = 8;       // largest interpolation width
+constexpr int kFftEpt = 16;    // complex elements held per thread in an FFT pass
+
+// ---------------------------------------------------------------- kernel psi
+// psi(u) = I0(beta sqrt(1 - (2u/J)^2)) on |u| < J/2 (open support).  With
+// z = 1 - (2u/J)^2 the power series of I0 gives psi = sum_k a_k z^k,
+// a_k = (beta^2/4)^k / (k!)^2: all terms positive on z in (0, 1].
+struct KbPoly {
+    float a[kKbTerms];   // a_k, zero-padded past the needed degree
+    float two_over_j;    // 2/J
+};
+
+__device__ __forceinline__ float kb_psi(const float* __restrict__ a, float two_over_j, float u) {
+    const float s = u * two_over_j;
+    const float z = fmaf(-s, s, 1.0f);
+    float acc = a[kKbTerms - 1];
+#pragma unroll
+    for (int k = kKbTerms - 2; k >= 0; --k) acc = fmaf(acc, z, a[k]);
+    return z > 0.f ? acc : 0.f;
+}
+
+// ---------------------------------------------------------- sorted points
+// Per point, per dim: wrapped window start k0 in [0, K) and the offset of the
+// first tap u0 = t - k0_unwrapped in [J/2 - 1, J/2); tap j has offset u0 - j.
+// idx.w holds the caller's point index.
+struct PointsView {
+    const int4* idx;     // {k0_0, k0_1, k0_2, original index}, sorted by bin
+    const float4* frac;  // {u0_0, u0_1, u0_2, 0}
+    int64_t m;
+};
+
+// ------------------------------------------------------------- FFT plans
+struct FftStage {
+    int R;          // radix
+    int Ns;         // product of the radices of the earlier stages
+    int tw_step;    // L / (Ns R): twiddle table stride
+    uint32_t magic; // ceil(2^32 / Ns) for Ns > 1 (division j / Ns)
+};
+
+struct FftAxis {
+    int L;
+    int nstages;
+    FftStage st[kMaxStages];
+    const float2* tw;   // exp(-2 pi i t / L), t < L (device)
+};
+
+__device__ __forceinline__ uint32_t div_magic(uint32_t n, uint32_t d, uint32_t magic) {
+    return d == 1 ? n : __umulhi(n, magic);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+}  // namespace nj

@@ -1,0 +1,346 @@
+// Shared-memory Stockham FFT passes over one axis of a channel-interleaved grid.
+//
+// Step (2) of the Appendix's NUFFT: a K-point FFT of the zero-padded, scaled
+// signal, applied one axis at a time.  A pass transforms every line of a
+// [B][L][S] array along its middle axis (S = stride of the faster axes,
+// channels innermost).  A block holds a tile of TB x TS lines in shared memory
+// as [L][TLP] (element-major, line-minor, TLP = TL + 1), so that consecutive
+// threads of a butterfly work on consecutive lines (conflict-free) and the
+// global loads and stores of a strided axis are coalesced along S.
+//
+// Stockham autosort, mixed radix (8, 4, 2, 3, 5): stage with radix R and
+// running length Ns reads a[j + r L/R], twiddles by W^(r (j mod Ns) L/(Ns R)),
+// takes an R-point DFT and writes b[(j div Ns) Ns R + (j mod Ns) + r Ns].
+// Stages alternate between two shared buffers (ping-pong), one butterfly per
+// thread at a time, so register use is independent of the tile size.
+//
+// Forward passes read N of the L input positions (zero padding: element e of
+// the image axis sits at position (e - N/2) mod L) and write all L; inverse
+// passes read all L and keep the N cropped positions.  The first forward pass
+// builds its input from the image (scaling s_n of the Appendix, coil map s_c
+// of Sec. II-G and coordinate weight r^[d] of Eq. (e,Ax)); the last inverse
+// pass applies the scaling, conj(s_c) and the coil sum.
+#include "internal.h"
+
+namespace nj {
+
+template <int DIR>
+__device__ __forceinline__ float2 mul_si(float2 z) {   // (DIR * i) * z
+    return DIR < 0 ? make_float2(z.y, -z.x) : make_float2(-z.y, z.x);
+}
+
+// In-register R-point DFT with exp(DIR * 2 pi i n k / R).
+template <int R, int DIR>
+struct Dft;
+
+template <int DIR>
+struct Dft<2, DIR> {
+    __device__ __forceinline__ static void run(float2* a) {
+        const float2 t = a[1];
+        a[1] = csub(a[0], t);
+        a[0] = cadd(a[0], t);
+    }
+};
+
+template <int DIR>
+struct Dft<4, DIR> {
+    __device__ __forceinline__ static void run(float2* a) {
+        const float2 t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+        const float2 t2 = cadd(a[1], a[3]), t3 = mul_si<DIR>(csub(a[1], a[3]));
+        a[0] = cadd(t0, t2);
+        a[2] = csub(t0, t2);
+        a[1] = cadd(t1, t3);
+        a[3] = csub(t1, t3);
+    }
+};
+
+template <int DIR>
+struct Dft<8, DIR> {
+    __device__ __forceinline__ static void run(float2* a) {
+        float2 e[4] = {a[0], a[2], a[4], a[6]};
+        float2 o[4] = {a[1], a[3], a[5], a[7]};
+        Dft<4, DIR>::run(e);
+        Dft<4, DIR>::run(o);
+        const float h = 0.70710678118654752f;
+        // o[k] *= exp(DIR 2 pi i k / 8)
+        o[1] = make_float2(h * (o[1].x - DIR * o[1].y), h * (o[1].y + DIR * o[1].x));
+        o[2] = mul_si<DIR>(o[2]);
+        o[3] = make_float2(h * (-o[3].x - DIR * o[3].y), h * (-o[3].y + DIR * o[3].x));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            a[k] = cadd(e[k], o[k]);
+            a[k + 4] = csub(e[k], o[k]);
+        }
+    }
+};
+
+template <int DIR>
+struct Dft<3, DIR> {
+    __device__ __forceinline__ static void run(float2* a) {
+        const float s3 = 0.86602540378443865f;   // sin(2 pi / 3)
+        const float2 t1 = cadd(a[1], a[2]);
+        const float2 t2 = cscale(mul_si<DIR>(csub(a[1], a[2])), s3);
+        const float2 m = make_float2(a[0].x - 0.5f * t1.x, a[0].y - 0.5f * t1.y);
+        a[0] = cadd(a[0], t1);
+        a[1] = cadd(m, t2);
+        a[2] = csub(m, t2);
+    }
+};
+
+template <int DIR>
+struct Dft<5, DIR> {
+    __device__ __forceinline__ static void run(float2* a) {
+        const float c1 = 0.30901699437494742f, c2 = -0.80901699437494742f;   // cos(2pi/5), cos(4pi/5)
+        const float s1 = 0.95105651629515357f, s2 = 0.58778525229247313f;    // sin(2pi/5), sin(4pi/5)
+        const float2 b1 = cadd(a[1], a[4]), b2 = cadd(a[2], a[3]);
+        const float2 d1 = csub(a[1], a[4]), d2 = csub(a[2], a[3]);
+        const float2 m1 = make_float2(a[0].x + c1 * b1.x + c2 * b2.x, a[0].y + c1 * b1.y + c2 * b2.y);
+        const float2 m2 = make_float2(a[0].x + c2 * b1.x + c1 * b2.x, a[0].y + c2 * b1.y + c1 * b2.y);
+        const float2 n1 = mul_si<DIR>(make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y));
+        const float2 n2 = mul_si<DIR>(make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y));
+        a[0] = cadd(a[0], cadd(b1, b2));
+        a[1] = cadd(m1, n1);
+        a[4] = csub(m1, n1);
+        a[2] = cadd(m2, n2);
+        a[3] = csub(m2, n2);
+    }
+};
+
+template <int R, int DIR>
+__device__ __forceinline__ void fft_stage(const float2* __restrict__ src, float2* __restrict__ dst,
+                                          const float2* __restrict__ tw, int L, int TLP, int lgTL, const FftStage st) {
+    const int LR = L / R;
+    const int TL = 1 << lgTL;
+    const int total = LR << lgTL;
+    const int sstride = LR * TLP, dstride = st.Ns * TLP;
+#pragma unroll 2
+    for (int u = threadIdx.x; u < total; u += blockDim.x) {
+        const int line = u & (TL - 1);
+        const int j = u >> lgTL;
+        const int jq = (int)div_magic((uint32_t)j, (uint32_t)st.Ns, st.magic);
+        const int kk = j - jq * st.Ns;
+        float2 v[R];
+        const float2* sp = src + j * TLP + line;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = sp[r * sstride];
+        if (st.Ns > 1) {
+            const int tstep = kk * st.tw_step;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = tw[r * tstep];
+                if (DIR > 0) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        Dft<R, DIR>::run(v);
+        float2* dp = dst + (jq * st.Ns * R + kk) * TLP + line;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dp[r * dstride] = v[r];
+    }
+    __syncthreads();
+}
+
+// Runs all stages; returns the buffer that holds the result.
+template <int DIR>
+__device__ float2* fft_all_stages(float2* buf0, float2* buf1, const float2* tw, const FftStage* sst, int nstages,
+                                  int L, int TLP, int lgTL) {
+    float2* src = buf0;
+    float2* dst = buf1;
+    for (int s = 0; s < nstages; ++s) {
+        const FftStage st = sst[s];
+        switch (st.R) {
+            case 8: fft_stage<8, DIR>(src, dst, tw, L, TLP, lgTL, st); break;
+            case 4: fft_stage<4, DIR>(src, dst, tw, L, TLP, lgTL, st); break;
+            case 2: fft_stage<2, DIR>(src, dst, tw, L, TLP, lgTL, st); break;
+            case 3: fft_stage<3, DIR>(src, dst, tw, L, TLP, lgTL, st); break;
+            default: fft_stage<5, DIR>(src, dst, tw, L, TLP, lgTL, st); break;
+        }
+        float2* t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
+// Row factors of an image line: scaling of the non-last dims and its
+// coordinates r^[d] = n_d - N_d/2 for d < D-1.
+__device__ __forceinline__ void image_row(int D, int N0, int N1, const float* deap0, const float* deap1, int64_t b,
+                                          float& scale, float& r0, float& r1) {
+    scale = 1.f;
+    r0 = r1 = 0.f;
+    if (D == 2) {
+        const int n0 = (int)b;
+        scale = deap0[n0];
+        r0 = (float)(n0 - N0 / 2);
+    } else if (D == 3) {
+        const int n0 = (int)(b / N1), n1 = (int)(b - (int64_t)n0 * N1);
+        scale = deap0[n0] * deap1[n1];
+        r0 = (float)(n0 - N0 / 2);
+        r1 = (float)(n1 - N1 / 2);
+    }
+}
+
+template <PassKind KIND>
+__global__ void __launch_bounds__(512) k_line_fft(LinePass a) {
+    constexpr int DIR = (KIND == PASS_FWD_FIRST || KIND == PASS_FWD_MID) ? -1 : 1;
+    extern __shared__ float2 smem[];
+    const int L = a.ax.L;
+    const int TS = a.TS, TB = a.TB, TL = TB * TS, TLP = a.TLP;
+    float2* tw = smem;
+    float2* buf = smem + L;
+    float2* buf1 = buf + (size_t)L * TLP;
+    float2* acc = buf1 + (size_t)L * TLP;                // coil-sum accumulator [TB][n_out]
+    float* row_scale = (float*)(acc + (a.coil_sum ? TB * a.n_out : 0));
+    float* row_r = row_scale + TB;                        // [TB][2]
+    __shared__ FftStage sst[kMaxStages];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * TB;
+
+    for (int i = tid; i < L; i += nt) tw[i] = a.ax.tw[i];
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < kMaxStages; ++i) sst[i] = a.ax.st[i];
+    }
+    if (KIND == PASS_FWD_FIRST || KIND == PASS_INV_LAST) {
+        for (int lb = tid; lb < TB; lb += nt) {
+            float sc = 0.f, r0 = 0.f, r1 = 0.f;
+            if (b0 + lb < a.B) image_row(a.im.D, a.im.N[0], a.im.N[1], a.im.deap[0], a.im.deap[1], b0 + lb, sc, r0, r1);
+            row_scale[lb] = sc;
+            row_r[2 * lb] = r0;
+            row_r[2 * lb + 1] = r1;
+        }
+    }
+    if (KIND == PASS_INV_LAST && a.coil_sum)
+        for (int i = tid; i < TB * a.n_out; i += nt) acc[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+
+    const int Dm1 = a.im.D - 1;
+    const int nlast = Dm1 == 2 ? a.im.N[2] : (Dm1 == 1 ? a.im.N[1] : a.im.N[0]);
+    const float* deap_last = Dm1 == 2 ? a.im.deap[2] : (Dm1 == 1 ? a.im.deap[1] : a.im.deap[0]);
+    const int nstages = a.ax.nstages;
+    const int half_in = a.n_in / 2;
+    const int nchunks = a.nchunks;
+
+    for (int chunk = 0; chunk < nchunks; ++chunk) {
+        const int64_t s0 = (a.coil_sum ? (int64_t)chunk : (int64_t)blockIdx.y) * TS;
+        // ---------------- prologue: fill the tile, zero padding included
+        const int nfill = L * TL;
+        for (int f = tid; f < nfill; f += nt) {
+            int p, lb, ls;
+            if (KIND == PASS_FWD_FIRST) {   // image side: positions fastest
+                const int line = (int)div_magic((uint32_t)f, (uint32_t)L, a.magic_L);
+                p = f - line * L;
+                lb = line >> a.lgTS;
+                ls = line & (TS - 1);
+            } else {                         // grid side: lines fastest
+                ls = f & (TS - 1);
+                const int rest = f >> a.lgTS;
+                lb = (int)div_magic((uint32_t)rest, (uint32_t)L, a.magic_L);
+                p = rest - lb * L;
+            }
+            int e;
+            if (DIR < 0) e = p < half_in ? p + half_in : (p >= L - half_in ? p - (L - half_in) : -1);
+            else e = p;
+            float2 val = make_float2(0.f, 0.f);
+            const int64_t b = b0 + lb, s = s0 + ls;
+            if (e >= 0 && b < a.B && s < a.S) {
+                if (KIND == PASS_FWD_FIRST) {
+                    const int dblk = (int)(s / a.im.C), c = (int)(s - (int64_t)dblk * a.im.C);
+                    const int kind = a.im.has_plain ? dblk - 1 : dblk;   // -1: plain image
+                    const int64_t pix = b * nlast + e;
+                    float2 xv = a.im.smaps ? cmul(a.im.x[pix], a.im.smaps[(int64_t)c * a.im.nimg + pix])
+                                           : a.im.x[(int64_t)c * a.im.nimg + pix];
+                    float sc = row_scale[lb] * deap_last[e];
+                    if (kind == Dm1) sc *= (float)(e - nlast / 2);
+                    else if (kind >= 0) sc *= row_r[2 * lb + kind];
+                    val = cscale(xv, sc);
+                } else {
+                    val = a.in[(b * a.n_in + e) * a.S + s];
+                }
+            }
+            buf[p * TLP + lb * TS + ls] = val;
+        }
+        __syncthreads();
+
+        const float2* res = fft_all_stages<DIR>(buf, buf1, tw, sst, nstages, L, TLP, a.lgTL);
+
+        // ---------------- epilogue
+        const int half_out = a.n_out / 2;
+        if (KIND == PASS_FWD_FIRST || KIND == PASS_FWD_MID || KIND == PASS_INV_MID) {
+            const int nst = a.n_out * TL;
+            for (int f = tid; f < nst; f += nt) {
+                const int ls = f & (TS - 1);
+                const int rest = f >> a.lgTS;
+                const int lb = (int)div_magic((uint32_t)rest, (uint32_t)a.n_out, a.magic_n);
+                const int e = rest - lb * a.n_out;
+                const int p = (DIR < 0) ? e : (e < half_out ? e + L - half_out : e - half_out);
+                const int64_t b = b0 + lb, s = s0 + ls;
+                if (b < a.B && s < a.S) a.out[(b * a.n_out + e) * a.S + s] = res[p * TLP + lb * TS + ls];
+            }
+        } else {   // PASS_INV_LAST: crop, scale, coil maps
+            if (a.coil_sum) {
+                const int nst = a.n_out * TB;
+                for (int f = tid; f < nst; f += nt) {
+                    const int lb = (int)div_magic((uint32_t)f, (uint32_t)a.n_out, a.magic_n);
+                    const int e = f - lb * a.n_out;
+                    const int p = e < half_out ? e + L - half_out : e - half_out;
+                    const int64_t b = b0 + lb;
+                    if (b >= a.B) continue;
+                    const int64_t pix = b * nlast + e;
+                    float2 sum = acc[lb * a.n_out + e];
+                    for (int ls = 0; ls < TS; ++ls) {
+                        const int64_t c = s0 + ls;
+                        if (c >= a.S) break;
+                        sum = cadd(sum, cmulc(res[p * TLP + lb * TS + ls], a.im.smaps[c * a.im.nimg + pix]));
+                    }
+                    acc[lb * a.n_out + e] = sum;
+                }
+            } else {
+                const int nst = a.n_out * TL;
+                for (int f = tid; f < nst; f += nt) {
+                    const int line = (int)div_magic((uint32_t)f, (uint32_t)a.n_out, a.magic_n);
+                    const int e = f - line * a.n_out;
+                    const int lb = line >> a.lgTS, ls = line & (TS - 1);
+                    const int p = e < half_out ? e + L - half_out : e - half_out;
+                    const int64_t b = b0 + lb, c = s0 + ls;
+                    if (b < a.B && c < a.S)
+                        a.im.xout[c * a.im.nimg + b * nlast + e] =
+                            cscale(res[p * TLP + lb * TS + ls], row_scale[lb] * deap_last[e]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (KIND == PASS_INV_LAST && a.coil_sum) {
+        for (int f = tid; f < TB * a.n_out; f += nt) {
+            const int lb = f / a.n_out, e = f - lb * a.n_out;
+            const int64_t b = b0 + lb;
+            if (b < a.B) a.im.xout[b * nlast + e] = cscale(acc[f], row_scale[lb] * deap_last[e]);
+        }
+    }
+}
+
+cudaError_t launch_line_pass(PassKind kind, const LinePass& a, dim3 grid, int threads, size_t smem,
+                             cudaStream_t s) {
+    switch (kind) {
+        case PASS_FWD_FIRST:
+            cudaFuncSetAttribute(k_line_fft<PASS_FWD_FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_line_fft<PASS_FWD_FIRST><<<grid, threads, smem, s>>>(a);
+            break;
+        case PASS_FWD_MID:
+            cudaFuncSetAttribute(k_line_fft<PASS_FWD_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_line_fft<PASS_FWD_MID><<<grid, threads, smem, s>>>(a);
+            break;
+        case PASS_INV_MID:
+            cudaFuncSetAttribute(k_line_fft<PASS_INV_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_line_fft<PASS_INV_MID><<<grid, threads, smem, s>>>(a);
+            break;
+        case PASS_INV_LAST:
+            cudaFuncSetAttribute(k_line_fft<PASS_INV_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_line_fft<PASS_INV_LAST><<<grid, threads, smem, s>>>(a);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace nj

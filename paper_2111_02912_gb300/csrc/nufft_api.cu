@@ -1,0 +1,729 @@
+// C ABI of libnufftjac: plans, tables, workspace and the orchestration of the
+// kernels for forward / adjoint / JVP / VJP (declarations in nufftjac.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/nufftjac.h"
+#include "internal.h"
+
+using namespace nj;
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<int64_t> g_launches{0};
+
+int fail(int status, const std::string& msg) {
+    g_last_error = msg;
+    return status;
+}
+
+#define NJ_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(NUFFT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+    } while (0)
+
+enum ProfKind {
+    PK_ZERO, PK_BIN_COUNT, PK_BIN_SCAN, PK_BIN_SCATTER, PK_BIN_SUBPROB, PK_FFT_FWD_FIRST, PK_FFT_FWD_MID,
+    PK_FFT_INV_MID, PK_FFT_INV_LAST, PK_GATHER_FWD, PK_GATHER_JVP, PK_GATHER_VJP, PK_SPREAD, PK_COUNT
+};
+const char* kProfNames[PK_COUNT] = {"zero", "bin_count", "bin_scan", "bin_scatter", "bin_subprob", "fft_fwd_first",
+                                    "fft_fwd_mid", "fft_inv_mid", "fft_inv_last", "gather_fwd", "gather_jvp",
+                                    "gather_vjp", "spread"};
+
+int64_t grid_size(int64_t n, double sigma) {
+    int64_t k = (int64_t)std::ceil(sigma * (double)n - 1e-9);
+    for (;; ++k) {
+        if (k % 2) continue;
+        int64_t q = k;
+        for (int p : {2, 3, 5})
+            while (q % p == 0) q /= p;
+        if (q == 1) return k;
+    }
+}
+
+int pow2_ceil(int64_t v) {
+    int p = 1;
+    while (p < v) p *= 2;
+    return p;
+}
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+uint32_t magic_of(uint32_t d) { return d <= 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + d - 1) / d); }
+
+}  // namespace
+
+struct nufft_plan_s {
+    int D = 0;
+    int64_t N[3] = {1, 1, 1}, K[3] = {1, 1, 1};
+    int J = 6;
+    double sigma = 2.0, beta = 0.0;
+    int maxC = 1;
+    int64_t M = 0, M_cap = 0;
+    int64_t Nimg = 1, Ktot = 1;
+    KbPoly kb{};
+    float* d_deap[3] = {nullptr, nullptr, nullptr};
+    float2* d_tw[3] = {nullptr, nullptr, nullptr};
+    FftAxis axis[3]{};
+    // bins
+    int B[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, T[3] = {1, 1, 1}, nbins = 1, P = 1024, CCmax = 1;
+    int* d_count = nullptr;
+    int* d_offsets = nullptr;
+    int* d_subp_off = nullptr;
+    int* d_nsubp = nullptr;
+    int4* d_subp = nullptr;
+    int* d_local = nullptr;
+    int* d_binid = nullptr;
+    int4* d_pidx = nullptr;
+    float4* d_pfrac = nullptr;
+    float c_hi[3] = {0, 0, 0}, c_lo[3] = {0, 0, 0};
+    // workspace
+    float2* d_G = nullptr;
+    float2* d_T = nullptr;
+    size_t G_elems = 0, T_elems = 0;
+    size_t bytes = 0;
+    cudaStream_t last_stream = nullptr;
+    // profiling
+    bool prof = false;
+    struct Ev {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Ev> events;
+    std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+cudaEvent_t get_event(nufft_plan_s* p) {
+    if (!p->pool.empty()) {
+        cudaEvent_t e = p->pool.back();
+        p->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Wraps one kernel launch: counts it and, when profiling, brackets it with events.
+template <typename F>
+int launch(nufft_plan_s* p, int kind, cudaStream_t s, F&& f) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (p->prof) {
+        a = get_event(p);
+        b = get_event(p);
+        cudaEventRecord(a, s);
+    }
+    cudaError_t e = f();
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (p->prof) {
+        cudaEventRecord(b, s);
+        p->events.push_back({kind, a, b});
+    }
+    if (e != cudaSuccess) return fail(NUFFT_ERR_CUDA, std::string("kernel ") + kProfNames[kind] + ": " + cudaGetErrorString(e));
+    return NUFFT_OK;
+}
+
+void build_fft_axis(int L, FftAxis& ax) {
+    std::vector<int> rad;
+    int q = L;
+    while (q % 8 == 0) { rad.push_back(8); q /= 8; }
+    while (q % 4 == 0) { rad.push_back(4); q /= 4; }
+    while (q % 2 == 0) { rad.push_back(2); q /= 2; }
+    while (q % 3 == 0) { rad.push_back(3); q /= 3; }
+    while (q % 5 == 0) { rad.push_back(5); q /= 5; }
+    ax.L = L;
+    ax.nstages = (int)rad.size();
+    int Ns = 1;
+    for (size_t i = 0; i < rad.size(); ++i) {
+        ax.st[i].R = rad[i];
+        ax.st[i].Ns = Ns;
+        ax.st[i].tw_step = L / (Ns * rad[i]);
+        ax.st[i].magic = magic_of((uint32_t)Ns);
+        Ns *= rad[i];
+    }
+}
+
+// Kaiser-Bessel Fourier transform int psi(u) exp(-2 pi i f u) du in closed form.
+double kb_ft(double f, int J, double beta) {
+    const double a = beta * beta - (M_PI * J * f) * (M_PI * J * f);
+    if (a > 0) { const double s = std::sqrt(a); return J * std::sinh(s) / s; }
+    if (a < 0) { const double s = std::sqrt(-a); return J * std::sin(s) / s; }
+    return J;
+}
+
+void free_plan(nufft_plan_s* p) {
+    for (int d = 0; d < 3; ++d) { cudaFree(p->d_deap[d]); cudaFree(p->d_tw[d]); }
+    cudaFree(p->d_count); cudaFree(p->d_offsets); cudaFree(p->d_subp_off); cudaFree(p->d_nsubp);
+    cudaFree(p->d_subp); cudaFree(p->d_local); cudaFree(p->d_binid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
+    cudaFree(p->d_G); cudaFree(p->d_T);
+    for (auto& e : p->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    for (auto e : p->pool) cudaEventDestroy(e);
+    delete p;
+}
+
+int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
+    if (!o) return fail(NUFFT_ERR_INVALID_ARG, "opts is NULL");
+    if (o->dim < 1 || o->dim > 3) return fail(NUFFT_ERR_UNSUPPORTED, "dim must be 1, 2 or 3");
+    p.D = o->dim;
+    p.sigma = o->sigma > 0 ? o->sigma : 2.0;
+    if (p.sigma <= 1.0 || p.sigma > 4.0) return fail(NUFFT_ERR_UNSUPPORTED, "sigma must lie in (1, 4]");
+    p.J = o->J ? o->J : 6;
+    if (p.J < 2 || p.J > kJMax) return fail(NUFFT_ERR_UNSUPPORTED, "J must lie in [2, 8]");
+    p.maxC = o->max_coils ? o->max_coils : 1;
+    if (p.maxC < 1 || p.maxC > 128) return fail(NUFFT_ERR_UNSUPPORTED, "max_coils must lie in [1, 128]");
+    p.Nimg = 1;
+    p.Ktot = 1;
+    for (int d = 0; d < p.D; ++d) {
+        const int64_t n = o->n[d];
+        if (n < 2 || n % 2) return fail(NUFFT_ERR_UNSUPPORTED, "every N_d must be even and >= 2");
+        p.N[d] = n;
+        p.K[d] = grid_size(n, p.sigma);
+        if (p.K[d] > 4096) return fail(NUFFT_ERR_UNSUPPORTED, "oversampled grid edge exceeds 4096");
+        if (p.K[d] < p.J) return fail(NUFFT_ERR_UNSUPPORTED, "oversampled grid edge smaller than J");
+        p.Nimg *= n;
+        p.Ktot *= p.K[d];
+    }
+    p.beta = o->beta > 0 ? o->beta
+                         : M_PI * std::sqrt(std::pow(p.J / p.sigma, 2) * std::pow(p.sigma - 0.5, 2) - 0.8);
+    // bins: tile edge B_d, tile extent B_d + J - 1 per dim; coils per spread block
+    const int defB[3][3] = {{512, 1, 1}, {32, 32, 1}, {16, 16, 8}};
+    size_t tcells = 1;
+    for (int d = 0; d < p.D; ++d) {
+        int b = o->bin_size[d] > 0 ? o->bin_size[d] : defB[p.D - 1][d];
+        b = (int)std::min<int64_t>(b, p.K[d]);
+        p.B[d] = b;
+        p.nb[d] = (int)((p.K[d] + b - 1) / b);
+        p.T[d] = b + p.J - 1;
+        tcells *= p.T[d];
+    }
+    p.nbins = 1;
+    for (int d = 0; d < p.D; ++d) p.nbins *= p.nb[d];
+    const size_t tile_budget = 96 * 1024;
+    const size_t wbytes = (256 * p.D * kJMax) * sizeof(float);
+    if (tcells * sizeof(float2) + wbytes > tile_budget + 16 * 1024)
+        return fail(NUFFT_ERR_UNSUPPORTED, "spread tile does not fit in shared memory; reduce bin_size");
+    p.CCmax = (int)std::max<size_t>(1, std::min<size_t>(32, tile_budget / (tcells * sizeof(float2))));
+    p.P = p.D == 3 ? 512 : 1024;
+    // KB power-series coefficients a_k = (beta^2/4)^k / (k!)^2
+    double ak = 1.0, sum = 0.0;
+    const double q = p.beta * p.beta / 4.0;
+    for (int k = 0; k < kKbTerms; ++k) {
+        if (k > 0) ak *= q / ((double)k * k);
+        p.kb.a[k] = (float)ak;
+        sum += ak;
+    }
+    if (ak > 1e-9 * sum) return fail(NUFFT_ERR_UNSUPPORTED, "beta too large for the kernel power series");
+    p.kb.two_over_j = (float)(2.0 / p.J);
+    for (int d = 0; d < p.D; ++d) {
+        const double c = (double)p.K[d] / (2.0 * M_PI);
+        p.c_hi[d] = (float)c;
+        p.c_lo[d] = (float)(c - (double)p.c_hi[d]);
+    }
+    return NUFFT_OK;
+}
+
+// Workspace element counts for max channels chmax = maxC (1 + D).
+void workspace_elems(const nufft_plan_s& p, size_t& G, size_t& T) {
+    const int64_t chmax = (int64_t)p.maxC * (1 + p.D);
+    G = (size_t)(p.Ktot * chmax);
+    T = 0;
+    // forward intermediates: after the pass over dim d, [N_0..N_{d-1}][K_d..K_{D-1}]
+    for (int d = p.D - 1; d >= 0; --d) {
+        int64_t n = 1;
+        for (int e = 0; e < d; ++e) n *= p.N[e];
+        for (int e = d; e < p.D; ++e) n *= p.K[e];
+        if ((d % 2) == 1) T = std::max<size_t>(T, (size_t)(n * chmax));
+        else G = std::max<size_t>(G, (size_t)(n * chmax));
+    }
+    // inverse intermediates: after the pass over dim d < D-1, [N_0..N_d][K_{d+1}..]
+    for (int d = 0; d < p.D - 1; ++d) {
+        int64_t n = 1;
+        for (int e = 0; e <= d; ++e) n *= p.N[e];
+        for (int e = d + 1; e < p.D; ++e) n *= p.K[e];
+        if ((d % 2) == 0) T = std::max<size_t>(T, (size_t)(n * p.maxC));
+        else G = std::max<size_t>(G, (size_t)(n * p.maxC));
+    }
+    if (T == 0) T = 1;
+}
+
+size_t point_bytes(const nufft_plan_s& p, int64_t cap) {
+    const size_t nsub = (size_t)p.nbins + (size_t)(cap / p.P) + 1;
+    return (size_t)cap * (2 * sizeof(int) + sizeof(int4) + sizeof(float4)) + nsub * sizeof(int4);
+}
+
+int alloc_points(nufft_plan_s* p, int64_t cap) {
+    cudaFree(p->d_subp); cudaFree(p->d_local); cudaFree(p->d_binid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
+    p->d_subp = nullptr; p->d_local = p->d_binid = nullptr; p->d_pidx = nullptr; p->d_pfrac = nullptr;
+    const size_t c = (size_t)std::max<int64_t>(cap, 1);
+    const size_t nsub = (size_t)p->nbins + (size_t)(cap / p->P) + 1;
+    if (cudaMalloc(&p->d_subp, nsub * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(&p->d_local, c * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&p->d_binid, c * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&p->d_pidx, c * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(&p->d_pfrac, c * sizeof(float4)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NUFFT_ERR_OOM, "device allocation of point arrays failed");
+    }
+    p->M_cap = cap;
+    return NUFFT_OK;
+}
+
+SortArgs sort_args(nufft_plan_s* p, const float* omega) {
+    SortArgs a{};
+    a.omega = omega;
+    a.m = p->M;
+    a.D = p->D;
+    a.J = p->J;
+    for (int d = 0; d < 3; ++d) {
+        a.K[d] = (int)p->K[d];
+        a.B[d] = p->B[d];
+        a.nb[d] = p->nb[d];
+        a.c_hi[d] = p->c_hi[d];
+        a.c_lo[d] = p->c_lo[d];
+    }
+    a.nbins = p->nbins;
+    a.P = p->P;
+    a.count = p->d_count;
+    a.local = p->d_local;
+    a.binid = p->d_binid;
+    a.offsets = p->d_offsets;
+    a.subp_off = p->d_subp_off;
+    a.subp = p->d_subp;
+    a.nsubp = p->d_nsubp;
+    a.pidx = p->d_pidx;
+    a.pfrac = p->d_pfrac;
+    return a;
+}
+
+int do_set_points(nufft_plan_s* p, int64_t m, const float* omega, cudaStream_t s) {
+    if (m < 0 || m > (int64_t)INT32_MAX) return fail(NUFFT_ERR_INVALID_ARG, "m out of range");
+    if (m > 0 && !omega) return fail(NUFFT_ERR_INVALID_ARG, "omega is NULL");
+    if (m > p->M_cap) {
+        NJ_CUDA(cudaStreamSynchronize(s));
+        int st = alloc_points(p, m);
+        if (st) return st;
+        p->bytes = 0;
+    }
+    p->M = m;
+    p->last_stream = s;
+    SortArgs a = sort_args(p, omega);
+    int st;
+    if ((st = launch(p, PK_ZERO, s, [&] { return launch_zero(p->d_count, sizeof(int) * p->nbins, s); }))) return st;
+    if ((st = launch(p, PK_BIN_COUNT, s, [&] { return launch_bin_count(a, s); }))) return st;
+    if ((st = launch(p, PK_BIN_SCAN, s, [&] { return launch_bin_scan(a, s); }))) return st;
+    if ((st = launch(p, PK_BIN_SCATTER, s, [&] { return launch_bin_scatter(a, s); }))) return st;
+    if ((st = launch(p, PK_BIN_SUBPROB, s, [&] { return launch_bin_subprob(a, s); }))) return st;
+    return NUFFT_OK;
+}
+
+// Tile shape of a line pass: TL lines (TB rows x TS channels) of length L.
+struct Tile {
+    int TB, TS, TL, threads;
+    size_t smem;
+};
+Tile pick_tile(int L, int64_t B, int64_t S, bool coil_sum, int n_out) {
+    const size_t budget = 100 * 1024;
+    int TL = 32;
+    while (TL > 1 && (size_t)(2 * (size_t)L * (TL + 1) + L) * sizeof(float2) > budget) TL /= 2;
+    Tile t;
+    t.TS = std::min<int>(TL, pow2_ceil(S));
+    t.TB = std::min<int>(TL / t.TS, pow2_ceil(B));
+    t.TL = t.TB * t.TS;
+    int work = (L / 2) * t.TL;   // butterflies of a radix-2 stage
+    t.threads = std::min(512, std::max(64, ((work + 31) / 32) * 32));
+    if (t.threads > 256 && work < 512) t.threads = 256;
+    t.smem = (size_t)(L + 2 * (size_t)L * (t.TL + 1)) * sizeof(float2) + (size_t)t.TB * 3 * sizeof(float);
+    if (coil_sum) t.smem += (size_t)t.TB * n_out * sizeof(float2);
+    return t;
+}
+
+ImageSide image_side(nufft_plan_s* p, int C, const float2* x, const float2* smaps, float2* xout, int has_plain) {
+    ImageSide im{};
+    im.x = x;
+    im.smaps = smaps;
+    im.xout = xout;
+    im.C = C;
+    im.has_plain = has_plain;
+    im.D = p->D;
+    for (int d = 0; d < 3; ++d) {
+        im.N[d] = (int)p->N[d];
+        im.deap[d] = p->d_deap[d] ? p->d_deap[d] : p->d_deap[0];
+    }
+    im.nimg = p->Nimg;
+    return im;
+}
+
+// Forward grids: channel (dblk, c) = dblk * C + c, dblk 0 = plain image when
+// has_plain, then r^[d]-weighted images.  Result in p->d_G, layout [K...][nd*C].
+int forward_grids(nufft_plan_s* p, int C, int nd, int has_plain, const float2* x, const float2* smaps, cudaStream_t s) {
+    const int D = p->D;
+    const int64_t ch = (int64_t)nd * C;
+    ImageSide im = image_side(p, C, x, smaps, nullptr, has_plain);
+    const float2* in = nullptr;
+    for (int k = 0; k < D; ++k) {
+        const int d = D - 1 - k;
+        const int L = (int)p->K[d];
+        int64_t B = 1, S = ch;
+        for (int e = 0; e < d; ++e) B *= p->N[e];
+        for (int e = d + 1; e < D; ++e) S *= p->K[e];
+        float2* out = (d % 2 == 0) ? p->d_G : p->d_T;
+        Tile t = pick_tile(L, B, S, false, L);
+        LinePass a{};
+        a.ax = p->axis[d];
+        a.n_in = (int)p->N[d];
+        a.n_out = L;
+        a.B = B;
+        a.S = S;
+        a.TB = t.TB;
+        a.TS = t.TS;
+        a.lgTS = ilog2(t.TS);
+        a.lgTL = ilog2(t.TL);
+        a.TLP = t.TL + 1;
+        a.nchunks = 1;
+        a.coil_sum = 0;
+        a.in = in;
+        a.out = out;
+        a.im = im;
+        a.magic_L = magic_of((uint32_t)L);
+        a.magic_n = magic_of((uint32_t)a.n_out);
+        dim3 grid((unsigned)((B + t.TB - 1) / t.TB), (unsigned)((S + t.TS - 1) / t.TS));
+        const PassKind kind = (k == 0) ? PASS_FWD_FIRST : PASS_FWD_MID;
+        int st = launch(p, k == 0 ? PK_FFT_FWD_FIRST : PK_FFT_FWD_MID, s,
+                        [&] { return launch_line_pass(kind, a, grid, t.threads, t.smem, s); });
+        if (st) return st;
+        in = out;
+    }
+    return NUFFT_OK;
+}
+
+// Adjoint of the interpolation + FFT + scaling for C coil channels of y.
+int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, float2* xout, cudaStream_t s) {
+    const int D = p->D;
+    int st;
+    const size_t gbytes = (size_t)p->Ktot * C * sizeof(float2);
+    if ((st = launch(p, PK_ZERO, s, [&] { return launch_zero(p->d_G, gbytes, s); }))) return st;
+    // spread
+    SpreadArgs sa{};
+    sa.pts = PointsView{p->d_pidx, p->d_pfrac, p->M};
+    sa.D = D;
+    sa.J = p->J;
+    for (int d = 0; d < 3; ++d) {
+        sa.K[d] = (int)p->K[d];
+        sa.B[d] = p->B[d];
+        sa.nb[d] = p->nb[d];
+        sa.T[d] = p->T[d];
+    }
+    sa.subp = p->d_subp;
+    sa.nsubp = p->d_nsubp;
+    sa.max_subp = p->M > 0 ? p->nbins + (int)(p->M / p->P) + 1 : 0;
+    sa.y = y;
+    sa.M = p->M;
+    sa.C = C;
+    sa.CC = std::min(C, p->CCmax);
+    sa.G = std::min(32, pow2_ceil(sa.CC));
+    sa.lgG = ilog2(sa.G);
+    const int cpl = (sa.CC + sa.G - 1) / sa.G;
+    sa.kb = p->kb;
+    sa.grid = p->d_G;
+    size_t tcells = 1;
+    for (int d = 0; d < D; ++d) tcells *= p->T[d];
+    const size_t ssm = tcells * sa.CC * sizeof(float2) + (size_t)(256 / sa.G) * D * kJMax * sizeof(float);
+    if ((st = launch(p, PK_SPREAD, s, [&] { return launch_spread(sa, cpl, s, ssm); }))) return st;
+    // inverse FFT passes, dim 0 first; the last one crops, scales and applies maps
+    const float2* in = p->d_G;
+    ImageSide im = image_side(p, C, nullptr, smaps, xout, 0);
+    for (int d = 0; d < D; ++d) {
+        const int L = (int)p->K[d];
+        int64_t B = 1, S = C;
+        for (int e = 0; e < d; ++e) B *= p->N[e];
+        for (int e = d + 1; e < D; ++e) S *= p->K[e];
+        const bool last = d == D - 1;
+        const bool coil_sum = last && smaps != nullptr;
+        float2* out = last ? nullptr : ((d % 2 == 0) ? p->d_T : p->d_G);
+        Tile t = pick_tile(L, B, S, coil_sum, (int)p->N[d]);
+        LinePass a{};
+        a.ax = p->axis[d];
+        a.n_in = L;
+        a.n_out = (int)p->N[d];
+        a.B = B;
+        a.S = S;
+        a.TB = t.TB;
+        a.TS = t.TS;
+        a.lgTS = ilog2(t.TS);
+        a.lgTL = ilog2(t.TL);
+        a.TLP = t.TL + 1;
+        a.coil_sum = coil_sum ? 1 : 0;
+        a.nchunks = coil_sum ? (int)((S + t.TS - 1) / t.TS) : 1;
+        a.in = in;
+        a.out = out;
+        a.im = im;
+        a.magic_L = magic_of((uint32_t)L);
+        a.magic_n = magic_of((uint32_t)a.n_out);
+        dim3 grid((unsigned)((B + t.TB - 1) / t.TB), coil_sum ? 1u : (unsigned)((S + t.TS - 1) / t.TS));
+        const PassKind kind = last ? PASS_INV_LAST : PASS_INV_MID;
+        st = launch(p, last ? PK_FFT_INV_LAST : PK_FFT_INV_MID, s,
+                    [&] { return launch_line_pass(kind, a, grid, t.threads, t.smem, s); });
+        if (st) return st;
+        in = out;
+    }
+    return NUFFT_OK;
+}
+
+GatherArgs gather_args(nufft_plan_s* p, int C, int nd, int has_plain) {
+    GatherArgs g{};
+    g.pts = PointsView{p->d_pidx, p->d_pfrac, p->M};
+    g.D = p->D;
+    g.J = p->J;
+    for (int d = 0; d < 3; ++d) g.K[d] = (int)p->K[d];
+    g.grid = p->d_G;
+    g.C = C;
+    g.nd = nd;
+    g.has_plain = has_plain;
+    g.G = std::min(32, pow2_ceil(C));
+    g.lgG = ilog2(g.G);
+    g.kb = p->kb;
+    g.M = p->M;
+    return g;
+}
+
+int check_call(nufft_plan_s* p, int C) {
+    if (!p) return fail(NUFFT_ERR_INVALID_ARG, "plan is NULL");
+    if (C < 1 || C > p->maxC) return fail(NUFFT_ERR_INVALID_ARG, "C must lie in [1, max_coils]");
+    return NUFFT_OK;
+}
+
+}  // namespace
+
+// =========================================================================== C ABI
+extern "C" {
+
+void nufft_default_opts(nufft_opts* o, int dim, const int64_t* n) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->dim = dim;
+    for (int d = 0; d < dim && d < 3 && n; ++d) o->n[d] = n[d];
+    o->sigma = 2.0;
+    o->J = 6;
+    o->beta = 0.0;
+    o->max_coils = 1;
+}
+
+size_t nufft_workspace_bytes(const nufft_opts* o, int64_t m) {
+    nufft_plan_s p;
+    if (validate_opts(o, p) != NUFFT_OK) return 0;
+    size_t G, T;
+    workspace_elems(p, G, T);
+    size_t b = (G + T) * sizeof(float2) + point_bytes(p, std::max<int64_t>(m, 1));
+    b += (size_t)(3 * p.nbins + 4) * sizeof(int);
+    for (int d = 0; d < p.D; ++d) b += (size_t)p.N[d] * sizeof(float) + (size_t)p.K[d] * sizeof(float2);
+    return b;
+}
+
+int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* omega, void* stream) {
+    if (!out) return fail(NUFFT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    nufft_plan_s* p = new (std::nothrow) nufft_plan_s();
+    if (!p) return fail(NUFFT_ERR_OOM, "host allocation failed");
+    int st = validate_opts(o, *p);
+    if (st) { delete p; return st; }
+    auto oom = [&](const char* what) {
+        cudaGetLastError();
+        free_plan(p);
+        return fail(NUFFT_ERR_OOM, std::string("device allocation failed: ") + what);
+    };
+    // tables: scaling factors s_d[n] = 1 / psi_hat((n - N/2) / K) and twiddles
+    for (int d = 0; d < p->D; ++d) {
+        std::vector<float> dp(p->N[d]);
+        for (int64_t n = 0; n < p->N[d]; ++n)
+            dp[n] = (float)(1.0 / kb_ft((double)(n - p->N[d] / 2) / (double)p->K[d], p->J, p->beta));
+        if (cudaMalloc(&p->d_deap[d], dp.size() * sizeof(float)) != cudaSuccess) return oom("scaling table");
+        cudaMemcpy(p->d_deap[d], dp.data(), dp.size() * sizeof(float), cudaMemcpyHostToDevice);
+        const int L = (int)p->K[d];
+        std::vector<float2> tw(L);
+        for (int t = 0; t < L; ++t) {
+            const double ang = -2.0 * M_PI * (double)t / (double)L;
+            tw[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+        if (cudaMalloc(&p->d_tw[d], L * sizeof(float2)) != cudaSuccess) return oom("twiddles");
+        cudaMemcpy(p->d_tw[d], tw.data(), L * sizeof(float2), cudaMemcpyHostToDevice);
+        build_fft_axis(L, p->axis[d]);
+        p->axis[d].tw = p->d_tw[d];
+    }
+    if (cudaMalloc(&p->d_count, sizeof(int) * p->nbins) != cudaSuccess ||
+        cudaMalloc(&p->d_offsets, sizeof(int) * (p->nbins + 1)) != cudaSuccess ||
+        cudaMalloc(&p->d_subp_off, sizeof(int) * (p->nbins + 1)) != cudaSuccess ||
+        cudaMalloc(&p->d_nsubp, sizeof(int)) != cudaSuccess)
+        return oom("bins");
+    cudaMemset(p->d_nsubp, 0, sizeof(int));
+    workspace_elems(*p, p->G_elems, p->T_elems);
+    if (cudaMalloc(&p->d_G, p->G_elems * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&p->d_T, p->T_elems * sizeof(float2)) != cudaSuccess)
+        return oom("workspace");
+    if ((st = alloc_points(p, std::max<int64_t>(m, 1)))) { free_plan(p); return st; }
+    if ((st = do_set_points(p, m, omega, (cudaStream_t)stream))) { free_plan(p); return st; }
+    *out = p;
+    return NUFFT_OK;
+}
+
+int nufft_set_points(nufft_plan_t p, int64_t m, const float* omega, void* stream) {
+    if (!p) return fail(NUFFT_ERR_INVALID_ARG, "plan is NULL");
+    return do_set_points(p, m, omega, (cudaStream_t)stream);
+}
+
+int nufft_forward(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cfloat* smaps, nufft_cfloat* y,
+                  void* stream) {
+    int st;
+    if ((st = check_call(p, C))) return st;
+    if (!x || (!y && p->M > 0)) return fail(NUFFT_ERR_INVALID_ARG, "x or y is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    if (p->M == 0) return NUFFT_OK;
+    if ((st = forward_grids(p, C, 1, 1, (const float2*)x, (const float2*)smaps, s))) return st;
+    GatherArgs g = gather_args(p, C, 1, 1);
+    g.y = (float2*)y;
+    const int cpl = (C + g.G - 1) / g.G;
+    return launch(p, PK_GATHER_FWD, s, [&] { return launch_gather(GM_FWD, g, cpl, s); });
+}
+
+int nufft_adjoint(nufft_plan_t p, int C, const nufft_cfloat* y, const nufft_cfloat* smaps, nufft_cfloat* x,
+                  void* stream) {
+    int st;
+    if ((st = check_call(p, C))) return st;
+    if (!x || (!y && p->M > 0)) return fail(NUFFT_ERR_INVALID_ARG, "x or y is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    return adjoint_impl(p, C, (const float2*)y, (const float2*)smaps, (float2*)x, s);
+}
+
+int nufft_jvp_omega(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cfloat* smaps, const float* domega,
+                    nufft_cfloat* dy, nufft_cfloat* y_or_null, void* stream) {
+    int st;
+    if ((st = check_call(p, C))) return st;
+    if (!x || (p->M > 0 && (!domega || !dy))) return fail(NUFFT_ERR_INVALID_ARG, "x, domega or dy is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    if (p->M == 0) return NUFFT_OK;
+    const int hp = y_or_null ? 1 : 0;
+    const int nd = p->D + hp;
+    if ((st = forward_grids(p, C, nd, hp, (const float2*)x, (const float2*)smaps, s))) return st;
+    GatherArgs g = gather_args(p, C, nd, hp);
+    g.y = (float2*)y_or_null;
+    g.dy = (float2*)dy;
+    g.domega = domega;
+    const int cpl = (C + g.G - 1) / g.G;
+    return launch(p, PK_GATHER_JVP, s, [&] { return launch_gather(GM_JVP, g, cpl, s); });
+}
+
+int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cfloat* smaps, const nufft_cfloat* v,
+                      float* grad_omega, nufft_cfloat* grad_x, void* stream) {
+    int st;
+    if ((st = check_call(p, C))) return st;
+    if ((p->M > 0 && !v) || (grad_omega && !x)) return fail(NUFFT_ERR_INVALID_ARG, "x or v is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    if (grad_omega && p->M > 0) {
+        if ((st = forward_grids(p, C, p->D, 0, (const float2*)x, (const float2*)smaps, s))) return st;
+        GatherArgs g = gather_args(p, C, p->D, 0);
+        g.v = (const float2*)v;
+        g.grad = grad_omega;
+        const int cpl = (C + g.G - 1) / g.G;
+        if ((st = launch(p, PK_GATHER_VJP, s, [&] { return launch_gather(GM_VJP, g, cpl, s); }))) return st;
+    }
+    if (grad_x) return adjoint_impl(p, C, (const float2*)v, (const float2*)smaps, (float2*)grad_x, s);
+    return NUFFT_OK;
+}
+
+int nufft_get_info(nufft_plan_t p, nufft_plan_info* info) {
+    if (!p || !info) return fail(NUFFT_ERR_INVALID_ARG, "plan or info is NULL");
+    std::memset(info, 0, sizeof(*info));
+    info->dim = p->D;
+    for (int d = 0; d < 3; ++d) {
+        info->n[d] = d < p->D ? p->N[d] : 1;
+        info->k[d] = d < p->D ? p->K[d] : 1;
+        info->bin_size[d] = d < p->D ? p->B[d] : 1;
+    }
+    info->J = p->J;
+    info->sigma = p->sigma;
+    info->beta = p->beta;
+    info->m = p->M;
+    info->nbins = p->nbins;
+    info->max_coils = p->maxC;
+    info->workspace_bytes = (p->G_elems + p->T_elems) * sizeof(float2) + point_bytes(*p, p->M_cap);
+    return NUFFT_OK;
+}
+
+void nufft_destroy(nufft_plan_t p) {
+    if (!p) return;
+    if (p->last_stream) cudaStreamSynchronize(p->last_stream);
+    else cudaDeviceSynchronize();
+    free_plan(p);
+}
+
+const char* nufft_status_string(int status) {
+    switch (status) {
+        case NUFFT_OK: return "ok";
+        case NUFFT_ERR_INVALID_ARG: return "invalid argument";
+        case NUFFT_ERR_UNSUPPORTED: return "unsupported configuration";
+        case NUFFT_ERR_OOM: return "out of device memory";
+        case NUFFT_ERR_CUDA: return "CUDA error";
+        case NUFFT_ERR_TIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+const char* nufft_last_error(void) { return g_last_error.c_str(); }
+
+int64_t nufft_launch_count(void) { return g_launches.load(); }
+
+int nufft_profile_enable(nufft_plan_t p, int enable) {
+    if (!p) return fail(NUFFT_ERR_INVALID_ARG, "plan is NULL");
+    p->prof = enable != 0;
+    return NUFFT_OK;
+}
+
+int nufft_profile_read(nufft_plan_t p, int max_kinds, const char** names, int* launches, double* total_ms,
+                       int* n_kinds) {
+    if (!p) return fail(NUFFT_ERR_INVALID_ARG, "plan is NULL");
+    int cnt[PK_COUNT] = {0};
+    double ms[PK_COUNT] = {0};
+    for (auto& e : p->events) {
+        cudaError_t r = cudaEventSynchronize(e.b);
+        if (r != cudaSuccess) return fail(NUFFT_ERR_CUDA, std::string("event sync: ") + cudaGetErrorString(r));
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e.a, e.b);
+        cnt[e.kind] += 1;
+        ms[e.kind] += t;
+        p->pool.push_back(e.a);
+        p->pool.push_back(e.b);
+    }
+    p->events.clear();
+    int k = 0;
+    for (int i = 0; i < PK_COUNT; ++i) {
+        if (!cnt[i]) continue;
+        if (k < max_kinds) {
+            if (names) names[k] = kProfNames[i];
+            if (launches) launches[k] = cnt[i];
+            if (total_ms) total_ms[k] = ms[i];
+        }
+        ++k;
+    }
+    if (n_kinds) *n_kinds = k;
+    return NUFFT_OK;
+}
+
+}  // extern "C"

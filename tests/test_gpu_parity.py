@@ -1,0 +1,188 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: rel-L2 1e-5 against the same-kernel FP64 NUFFT, 5e-4 against the
+exact NUDFT, 1e-3 for grad_omega against the exact Jacobian.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import host, make_case, rel, to_dev
+from oracle import jacobian as jb
+from oracle.nudft import NUDFT
+from oracle.nufft import KBNufft
+
+pytestmark = pytest.mark.gpu
+
+TOL_SAME = 1e-5
+TOL_EXACT = 5e-4
+TOL_GRAD_EXACT = 1e-3
+
+CASES = [
+    # name, shape, M, C, maps, opts
+    ("1d", (64,), 700, 1, False, {}),
+    ("2d_maps", (32, 40), 1500, 3, True, {}),
+    ("2d_multi_image", (24, 18), 900, 5, False, {}),
+    ("2d_small64", (64, 64), 4096, 1, False, {}),
+    ("2d_many_coils", (16, 16), 600, 40, True, {}),
+    ("2d_low_accuracy", (40, 48), 1200, 2, True, dict(J=5, sigma=1.25)),
+    ("2d_ragged", (30, 22), 37, 2, True, {}),
+    ("3d_maps", (16, 20, 12), 2000, 2, True, {}),
+    ("3d_multi_image", (12, 10, 14), 800, 3, False, {}),
+]
+
+
+def _plan(case, **opts):
+    from paper_2111_02912_gb300 import Plan
+    return Plan(case["shape"], to_dev(case["omega"]), max_coils=case["C"], **opts)
+
+
+@pytest.mark.parametrize("name,shape,M,C,maps,opts", CASES, ids=[c[0] for c in CASES])
+def test_all_products_match_same_kernel_oracle(name, shape, M, C, maps, opts):
+    import torch
+    case = make_case(shape, M, C, maps, seed=sum(map(ord, name)))
+    plan = _plan(case, **opts)
+    X, S, V, Y, DOM = (to_dev(case[k]) for k in ("x", "smaps", "v", "y", "domega"))
+    y = plan.forward(X, S)
+    xa = plan.adjoint(Y, S)
+    dy, y2 = plan.jvp_omega(X, DOM, S, want_y=True)
+    dy_only = plan.jvp_omega(X, DOM, S)
+    go, gx = plan.vjp_omega_x(X, V, S)
+    torch.cuda.synchronize()
+    op = KBNufft(shape, case["omega"], **opts)
+    s = case["smaps"]
+    y_ref = jb.sense_forward(op, case["x"], s)
+    assert rel(host(y), y_ref) < TOL_SAME
+    assert rel(host(y2), y_ref) < TOL_SAME
+    assert rel(host(xa), jb.sense_adjoint(op, case["y"], s)) < TOL_SAME
+    dy_ref = jb.jvp_omega(op, case["x"], case["domega"], s)
+    assert rel(host(dy), dy_ref) < TOL_SAME
+    assert rel(host(dy_only), dy_ref) < TOL_SAME
+    go_ref, gx_ref = jb.vjp_omega_x(op, case["x"], case["v"], s)
+    assert rel(host(go), go_ref) < TOL_SAME
+    assert rel(host(gx), gx_ref) < TOL_SAME
+
+
+def test_small64_against_exact_nudft_and_jacobian():
+    """64x64, M = 4096 uniform omega: the method's own accuracy (Appendix bounds) at FP32."""
+    import torch
+    case = make_case((64, 64), 4096, 1, False, seed=7)
+    plan = _plan(case)
+    X, V = to_dev(case["x"]), to_dev(case["v"])
+    y = plan.forward(X)
+    go, gx = plan.vjp_omega_x(X, V)
+    torch.cuda.synchronize()
+    ex = NUDFT((64, 64), case["omega"])
+    assert rel(host(y), jb.sense_forward(ex, case["x"])) < TOL_EXACT
+    go_ref, gx_ref = jb.vjp_omega_x(ex, case["x"], case["v"])
+    assert rel(host(go), go_ref) < TOL_GRAD_EXACT
+    assert rel(host(gx), gx_ref) < TOL_EXACT
+
+
+def test_radial320_full_size_parity():
+    """The 320x320, 16-coil, 80 golden-angle spokes x 640 workload, full size, every output."""
+    import torch
+
+    from paper_2111_02912_gb300 import Plan
+    from paper_2111_02912_gb300.workloads import workload
+    w = workload("radial320")
+    g = np.random.default_rng(5)
+    C, M = w["C"], w["omega"].shape[1]
+    v = (g.standard_normal((C, M)) + 1j * g.standard_normal((C, M))).astype(np.complex64)
+    plan = Plan(w["shape"], to_dev(w["omega"]), max_coils=C)
+    X, S, V = to_dev(w["x"]), to_dev(w["smaps"]), to_dev(v)
+    y = plan.forward(X, S)
+    go, gx = plan.vjp_omega_x(X, V, S)
+    torch.cuda.synchronize()
+    op = KBNufft(w["shape"], w["omega"])
+    assert rel(host(y), jb.sense_forward(op, w["x"], w["smaps"])) < TOL_SAME
+    go_ref, gx_ref = jb.vjp_omega_x(op, w["x"], v, w["smaps"])
+    assert rel(host(go), go_ref) < TOL_SAME
+    assert rel(host(gx), gx_ref) < TOL_SAME
+    # exact NUDFT on a point subset (the exact sum is O(MN) per coil)
+    sub = np.arange(0, M, 25)
+    ex = NUDFT(w["shape"], w["omega"][:, sub])
+    assert rel(host(y)[:, sub], jb.sense_forward(ex, w["x"], w["smaps"])) < TOL_EXACT
+    ge, _ = jb.vjp_omega_x(ex, w["x"], v[:, sub], w["smaps"])
+    assert rel(host(go)[:, sub], ge) < TOL_GRAD_EXACT
+
+
+def test_empty_and_single_point():
+    import torch
+    case = make_case((16, 16), 0, 2, True, seed=3)
+    plan = _plan(case)
+    X, S = to_dev(case["x"]), to_dev(case["smaps"])
+    y = plan.forward(X, S)
+    xa = plan.adjoint(to_dev(np.zeros((2, 0), np.complex64)), S)
+    torch.cuda.synchronize()
+    assert y.shape == (2, 0) and float(xa.abs().max()) == 0.0
+    one = make_case((16, 16), 1, 2, True, seed=4)
+    plan.set_points(to_dev(one["omega"]))
+    y1 = plan.forward(X, S)
+    torch.cuda.synchronize()
+    assert rel(host(y1), jb.sense_forward(KBNufft((16, 16), one["omega"]), case["x"], case["smaps"])) < TOL_SAME
+
+
+def test_periodic_omega_and_boundary_values():
+    """omega shifted by multiples of 2 pi, and omega exactly at -pi / on grid points."""
+    import torch
+    g = np.random.default_rng(11)
+    M = 1000
+    om = g.uniform(-np.pi, np.pi, (2, M)).astype(np.float32)
+    om[:, :10] = -np.float32(np.pi)
+    om[:, 10:20] = (2 * np.pi * g.integers(-32, 32, (2, 10)) / 64).astype(np.float32)
+    case = make_case((32, 32), M, 2, True, seed=5, omega=om)
+    plan = _plan(case)
+    X, S = to_dev(case["x"]), to_dev(case["smaps"])
+    y = host(plan.forward(X, S))
+    shifted = (om + np.float32(2 * np.pi) * g.integers(-3, 4, om.shape).astype(np.float32)).astype(np.float32)
+    plan.set_points(to_dev(shifted))
+    y_s = host(plan.forward(X, S))
+    torch.cuda.synchronize()
+    ref = jb.sense_forward(KBNufft((32, 32), om), case["x"], case["smaps"])
+    assert rel(y, ref) < TOL_SAME
+    ref_s = jb.sense_forward(KBNufft((32, 32), shifted), case["x"], case["smaps"])
+    assert rel(y_s, ref_s) < TOL_SAME
+
+
+def test_adjoint_identity_in_fp32():
+    import torch
+    case = make_case((48, 40), 3000, 4, True, seed=6)
+    plan = _plan(case)
+    X, S, Y = to_dev(case["x"]), to_dev(case["smaps"]), to_dev(case["y"])
+    lhs = torch.vdot(Y.flatten(), plan.forward(X, S).flatten())
+    rhs = torch.vdot(plan.adjoint(Y, S).flatten(), X.flatten())
+    assert abs(complex(lhs) - complex(rhs)) < 1e-5 * abs(complex(lhs))
+
+
+def test_gather_is_deterministic_and_resort_is_consistent():
+    import torch
+    case = make_case((40, 40), 5000, 3, True, seed=8)
+    plan = _plan(case)
+    X, S, V = to_dev(case["x"]), to_dev(case["smaps"]), to_dev(case["v"])
+    a = plan.forward(X, S).clone()
+    plan.set_points(to_dev(case["omega"]))
+    b = plan.forward(X, S).clone()
+    g1, x1 = plan.vjp_omega_x(X, V, S)
+    g2, x2 = plan.vjp_omega_x(X, V, S)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(g1, g2)
+    assert rel(host(x1), host(x2)) < 1e-6        # spread: atomics reorder rounding only
+
+
+def test_launch_counter_and_profile_hooks():
+    import torch
+
+    from paper_2111_02912_gb300 import nufft_launch_count
+    case = make_case((32, 32), 2000, 2, True, seed=9)
+    plan = _plan(case)
+    X, S, V = to_dev(case["x"]), to_dev(case["smaps"]), to_dev(case["v"])
+    plan.profile_enable(True)
+    n0 = nufft_launch_count()
+    plan.forward(X, S)
+    plan.vjp_omega_x(X, V, S)
+    n1 = nufft_launch_count()
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    assert n1 - n0 == sum(v[0] for v in prof.values())
+    assert {"fft_fwd_first", "fft_fwd_mid", "gather_fwd", "gather_vjp", "spread", "fft_inv_last"} <= set(prof)
+    assert all(ms > 0 for _, ms in prof.values())
