@@ -1,0 +1,380 @@
+"""Benchmark of the NUFFT-Jacobian hot path on the radial 320x320, 16-coil workload.
+
+One step = nufft_set_points (bin sort of omega) + nufft_forward (y = E x) +
+nufft_vjp_omega_x (grad_omega by the fused interpolation epilogue, grad_x =
+E' v by the tiled spread): every row of the hot path on one batch.
+Throughput unit: non-uniform points x channels per second, with channels =
+C (1 + D) per step (C coils, the plain image plus D coordinate-weighted
+images per coil).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (weak scaling); rank 0
+prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NU-pts*channels/s & % HBM roofline, batched Jacobian vs plain path; p50/p99 ms"
+UNIT = "NU-pts*channels/s"
+WORKLOAD = ("radial320: 320x320 complex64 image, 16 Gaussian-bump coil maps, 80 golden-angle spokes x 640 "
+            "readout = 51200 points, Kaiser-Bessel J=6, sigma=2 (640x640 grid); step = set_points + forward "
+            "+ vjp(grad_omega, grad_x)")
+FALLBACK_HBM = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+# ------------------------------------------------------------------ workload
+def make_inputs():
+    from paper_2111_02912_gb300.workloads import workload
+    w = workload("radial320")
+    C, M = w["C"], w["omega"].shape[1]
+    g = np.random.default_rng(2111_02912 + 101)
+    v = ((g.standard_normal((C, M)) + 1j * g.standard_normal((C, M))) / math.sqrt(2)).astype(np.complex64)
+    w["v"] = v
+    return w
+
+
+def touched_cells(omega, K, J):
+    """Grid cells inside some sample's J-tap window (algorithmic grid footprint U)."""
+    D, M = omega.shape
+    starts = []
+    for d in range(D):
+        t = omega[d].astype(np.float64) * K[d] / (2 * np.pi)
+        starts.append(np.floor(t - J / 2.0).astype(np.int64) + 1)
+    lin = np.zeros((M, 1), dtype=np.int64)
+    for d in range(D):
+        k = np.mod(starts[d][:, None] + np.arange(J)[None, :], K[d])
+        lin = (lin[:, :, None] * K[d] + k[:, None, :]).reshape(M, -1)
+    return int(np.unique(lin).size)
+
+
+def algorithmic_bytes(w, info):
+    """Bytes each kernel kind must move per launch (inputs read once, outputs written once)."""
+    N = [info.n[d] for d in range(2)]
+    K = [info.k[d] for d in range(2)]
+    C, M, D = w["C"], w["omega"].shape[1], 2
+    U = touched_cells(w["omega"], K, info.J)
+    c8 = 8
+    Nimg, Kt = N[0] * N[1], K[0] * K[1]
+    fwd_first = lambda ch: Nimg * c8 + C * Nimg * c8 + N[0] * K[1] * ch * c8
+    fwd_mid = lambda ch: N[0] * K[1] * ch * c8 + Kt * ch * c8
+    return {
+        # forward (ch = C) and VJP (ch = C D) launches of the same kinds, averaged per launch
+        "fft_fwd_first": (fwd_first(C) + fwd_first(C * D)) / 2,
+        "fft_fwd_mid": (fwd_mid(C) + fwd_mid(C * D)) / 2,
+        "gather_fwd": U * C * c8 + M * D * 4 + M * C * c8,
+        "gather_vjp": U * C * D * c8 + M * D * 4 + M * C * c8 + M * D * 4,
+        "spread": M * C * c8 + M * D * 4 + U * C * c8,
+        "zero": Kt * C * c8,
+        "fft_inv_mid": Kt * C * c8 + N[0] * K[1] * C * c8,
+        "fft_inv_last": N[0] * K[1] * C * c8 + C * Nimg * c8 + Nimg * c8,
+        "bin_count": M * D * 4 + M * 8, "bin_scatter": M * D * 4 + M * 8 + M * 32,
+    }, U
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+
+    from paper_2111_02912_gb300 import Plan, nufft_launch_count
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = make_inputs()
+    C, M, D = w["C"], w["omega"].shape[1], 2
+    units = M * C * (1 + D)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    om, X, S, V = t(w["omega"]), t(w["x"]), t(w["smaps"]), t(w["v"])
+    plan = Plan(w["shape"], om, max_coils=C)
+    y = torch.empty((C, M), dtype=torch.complex64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.set_points(om)
+        plan.forward(X, S, out=y)
+        return plan.vjp_omega_x(X, V, S)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+
+    def timed_region(profile):
+        plan.profile_enable(profile)
+        if profile:
+            plan.profile_read()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        barrier()
+        n0 = nufft_launch_count()
+        for a, b in evs:
+            flush.fill_(1.0)                 # evict L2 between steps (outside the events)
+            a.record(stream)
+            step()
+            b.record(stream)
+        barrier()
+        n1 = nufft_launch_count()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        prof = plan.profile_read() if profile else None
+        plan.profile_enable(False)
+        return ms, n1 - n0, prof
+
+    with ClockSampler(local) as clk:
+        ms, launches, _ = timed_region(False)
+    clocks = clk.summary()
+    total_ms = float(sum(ms))
+    if ws > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = ws * units * args.steps / (total_ms / 1e3)
+
+    # kernel roofline: the same timed region with per-kernel events on the launching stream
+    ms_p, _, prof = timed_region(True)
+    info = plan.info()
+    algo, U = algorithmic_bytes(w, info)
+    hbm, hbm_src = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, kms) = dom
+    per_launch_ms = kms / nl
+    achieved = algo.get(name, 0.0) / (per_launch_ms / 1e3) / 1e9
+    roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)"
+            if hbm_src == "measured" else "fallback",
+            "traffic": traffic_for(name), "algorithmic_bytes_per_launch": int(algo.get(name, 0)),
+            "launch_ms": round(per_launch_ms, 5), "share_of_step": round(kms / sum(v[1] for v in prof.values()), 3),
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 4), "gbs": round(algo[k] * v[0] / (v[1] / 1e3) / 1e9, 1)
+                            if k in algo else None} for k, v in prof.items()},
+            "profiled_ms_per_step": round(float(np.mean(ms_p)), 5), "U_cells": U}
+
+    # end to end through the public API from pinned host memory
+    hx = torch.from_numpy(w["x"]).pin_memory()
+    hs = torch.from_numpy(w["smaps"]).pin_memory()
+    hom = torch.from_numpy(w["omega"]).pin_memory()
+    hv = torch.from_numpy(w["v"]).pin_memory()
+    hy = torch.empty((C, M), dtype=torch.complex64).pin_memory()
+    hgo = torch.empty((D, M), dtype=torch.float32).pin_memory()
+    hgx = torch.empty(w["shape"], dtype=torch.complex64).pin_memory()
+    h2d = sum(a.numel() * a.element_size() for a in (hx, hs, hom, hv))
+    d2h = sum(a.numel() * a.element_size() for a in (hy, hgo, hgx))
+
+    def e2e_step():
+        om.copy_(hom, non_blocking=True)
+        X.copy_(hx, non_blocking=True)
+        S.copy_(hs, non_blocking=True)
+        V.copy_(hv, non_blocking=True)
+        go, gx = step()
+        hy.copy_(y, non_blocking=True)
+        hgo.copy_(go, non_blocking=True)
+        hgx.copy_(gx, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for a, b in evs:
+        flush.fill_(1.0)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+    barrier()
+    e2e_ms = float(sum(a.elapsed_time(b) for a, b in evs))
+    if ws > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e = {"value": ws * units * args.steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 complex)",
+            "data": "synthetic (seeded; shapes of the paper's 2-D multicoil radial case)",
+            "config": {"workload": WORKLOAD, "points": M, "coils": C, "channels_per_step": C * (1 + D),
+                       "units_per_step": units, "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic_radial320.txt")
+    if not os.path.exists(path):
+        return None
+    src = source_hash()
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 3 and f[0] == kernel and f[2] == src:
+            return int(float(f[1]))
+    return None
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for name in ("kernels_fft.cu", "kernels_interp.cu", "kernels_sort.cu", "common.cuh", "nufft_api.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2111_02912_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_step(w, coils):
+    """The oracle's FP64 same-kernel NUFFT on the same step, restricted to `coils` coils."""
+    from oracle import jacobian as jb
+    from oracle.nufft import KBNufft
+    S = w["smaps"][:coils]
+    v = w["v"][:coils]
+    op = KBNufft(w["shape"], w["omega"])           # plan = window geometry (set_points)
+    jb.sense_forward(op, w["x"], S)
+    jb.vjp_omega_x(op, w["x"], v, S)
+
+
+def cpu_baseline(w, coils=2, reps=3):
+    M, D = w["omega"].shape[1], 2
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle_step(w, coils)
+        times.append(time.perf_counter() - t0)
+    t = float(np.median(times))
+    return {"value": M * coils * (1 + D) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "radial320 step restricted to %d of 16 coils (all 51200 points), median of %d; "
+                      "NumPy FFT and interpolation run on one host thread" % (coils, reps)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w = make_inputs()
+    M, D, coils = w["omega"].shape[1], 2, 1
+    for _ in range(args.warmup):
+        oracle_step(w, coils)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(w, coils)
+        times.append(time.perf_counter() - t0)
+    total = float(sum(times))
+    units = M * coils * (1 + D)
+    value = units * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "each step: 1 of 16 coils, all 51200 points"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "radial320 step, 1 of 16 coils, all points"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
