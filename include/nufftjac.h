@@ -130,6 +130,29 @@ void nufft_destroy(nufft_plan_t p);
 const char* nufft_status_string(int status);
 const char* nufft_last_error(void);
 
+/* ---- allocation-free forward (the paper has no counterpart) --------------
+ * For callers that cannot allocate device memory: code whose device memory is
+ * owned by another allocator (a framework's caching allocator, a service with
+ * a fixed memory budget) or that must not allocate while it runs.  Same result
+ * as nufft_plan + nufft_forward on the same arguments, but without a plan: all
+ * scratch (scaling and twiddle tables, the bin sort, the FFT workspace) lives
+ * in one file-scope device array of NUFFT_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading this library holds until the process exits.  The call allocates
+ * nothing (no cudaMalloc / cudaFree, no allocating library routine).
+ *   - o, m, omega, C, x, smaps, y as for nufft_plan / nufft_forward.
+ *   - A problem whose scratch would exceed the array returns
+ *     NUFFT_ERR_UNSUPPORTED with the byte counts in nufft_last_error().
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call uses the same array and leaves its contents behind; calls
+ *     whose work overlaps on the GPU (other streams, other host threads)
+ *     race on it and must be serialised by the caller.  The call itself
+ *     zeroes what must start at zero (the sort counters).
+ *   - Tables are copied from host memory with cudaMemcpyAsync on `stream`. */
+#define NUFFT_NOALLOC_SCRATCH_BYTES (32u << 20)
+int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float* omega, int C, const nufft_cfloat* x,
+                          const nufft_cfloat* smaps, nufft_cfloat* y, void* stream);
+
 /* ---- measurement hooks -------------------------------------------------
  * Kernel launches made by this library in this process (all plans). */
 int64_t nufft_launch_count(void);

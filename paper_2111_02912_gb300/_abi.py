@@ -20,8 +20,10 @@ EXPORTED = (
     "nufft_default_opts", "nufft_plan", "nufft_set_points", "nufft_forward", "nufft_adjoint",
     "nufft_jvp_omega", "nufft_vjp_omega_x", "nufft_workspace_bytes", "nufft_get_info", "nufft_destroy",
     "nufft_status_string", "nufft_last_error", "nufft_launch_count", "nufft_profile_enable",
-    "nufft_profile_read",
+    "nufft_profile_read", "nufft_forward_noalloc",
 )
+
+NUFFT_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class nufft_opts(ctypes.Structure):
@@ -63,6 +65,8 @@ def lib():
         L.nufft_adjoint.argtypes = [vp, i32, vp, vp, vp, vp]
         L.nufft_jvp_omega.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
         L.nufft_vjp_omega_x.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
+        L.nufft_forward_noalloc.argtypes = [ctypes.POINTER(nufft_opts), i64, vp, i32, vp, vp, vp, vp]
+        L.nufft_forward_noalloc.restype = i32
         L.nufft_workspace_bytes.argtypes = [ctypes.POINTER(nufft_opts), i64]
         L.nufft_workspace_bytes.restype = ctypes.c_size_t
         L.nufft_get_info.argtypes = [vp, ctypes.POINTER(nufft_plan_info)]
@@ -157,3 +161,8 @@ def nufft_profile_read(plan, max_kinds=32):
     n = ctypes.c_int()
     _check(lib().nufft_profile_read(plan, max_kinds, names, launches, ms, ctypes.byref(n)), "nufft_profile_read")
     return {names[i].decode(): (launches[i], ms[i]) for i in range(min(n.value, max_kinds))}
+
+
+def nufft_forward_noalloc(opts, m, omega_ptr, C, x, smaps, y, stream=0):
+    _check(lib().nufft_forward_noalloc(ctypes.byref(opts), int(m), omega_ptr, int(C), x, smaps, y, stream),
+           "nufft_forward_noalloc")

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -727,3 +728,131 @@ int nufft_profile_read(nufft_plan_t p, int max_kinds, const char** names, int* l
 }
 
 }  // extern "C"
+
+// ============================================================ allocation-free forward
+// nufft_forward_noalloc: the forward NUFFT without a plan and without any
+// device allocation.  For callers that cannot call cudaMalloc: code that runs
+// under a device-memory budget owned by another allocator (a framework's
+// caching allocator, a real-time or embedded service with a fixed footprint),
+// or that must not allocate while it runs.  All scratch (tables, bin sort,
+// FFT workspace) is carved from one file-scope device array of
+// NUFFT_NOALLOC_SCRATCH_BYTES; every GPU that loads this library holds it
+// until the process exits.
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NUFFT_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array for the current device (looked up once
+// per device, with that device current).
+int noalloc_scratch(void** out) {
+    int dev = 0;
+    NJ_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(NUFFT_ERR_UNSUPPORTED, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(NUFFT_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return NUFFT_OK;
+}
+
+struct Carve {
+    size_t off = 0;
+    template <typename T>
+    size_t take(size_t n) {
+        const size_t at = off;
+        off = (off + n * sizeof(T) + 255) / 256 * 256;
+        return at;
+    }
+};
+
+}  // namespace
+
+extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float* omega, int C,
+                                     const nufft_cfloat* x, const nufft_cfloat* smaps, nufft_cfloat* y,
+                                     void* stream) {
+    nufft_plan_s p;   // host-side description only; every device pointer below is scratch
+    int st = validate_opts(o, p);
+    if (st) return st;
+    if (C < 1 || C > 128) return fail(NUFFT_ERR_INVALID_ARG, "C must lie in [1, 128]");
+    if (m < 0 || m > (int64_t)INT32_MAX) return fail(NUFFT_ERR_INVALID_ARG, "m out of range");
+    if (m > 0 && (!omega || !x || !y)) return fail(NUFFT_ERR_INVALID_ARG, "omega, x or y is NULL");
+    p.maxC = C;
+    // forward workspace for C channels: the pass over dim d leaves [N_0..N_{d-1}][K_d..][C]
+    size_t G = (size_t)p.Ktot * C, T = 1;
+    for (int d = p.D - 1; d >= 0; --d) {
+        int64_t n = C;
+        for (int e = 0; e < d; ++e) n *= p.N[e];
+        for (int e = d; e < p.D; ++e) n *= p.K[e];
+        if (d % 2) T = std::max<size_t>(T, (size_t)n);
+        else G = std::max<size_t>(G, (size_t)n);
+    }
+    const int64_t mc = std::max<int64_t>(m, 1);
+    Carve cv;
+    size_t o_deap[3], o_tw[3];
+    for (int d = 0; d < p.D; ++d) {
+        o_deap[d] = cv.take<float>(p.N[d]);
+        o_tw[d] = cv.take<float2>(p.K[d]);
+    }
+    const size_t o_count = cv.take<int>(p.nbins), o_offsets = cv.take<int>(p.nbins + 1),
+                 o_subp_off = cv.take<int>(p.nbins + 1), o_nsubp = cv.take<int>(1),
+                 o_subp = cv.take<int4>((size_t)p.nbins + (size_t)(mc / p.P) + 1), o_local = cv.take<int>(mc),
+                 o_binid = cv.take<int>(mc), o_pidx = cv.take<int4>(mc), o_pfrac = cv.take<float4>(mc),
+                 o_G = cv.take<float2>(G), o_T = cv.take<float2>(T);
+    if (cv.off > (size_t)NUFFT_NOALLOC_SCRATCH_BYTES)
+        return fail(NUFFT_ERR_UNSUPPORTED, "problem needs " + std::to_string(cv.off) +
+                                               " bytes of scratch; nufft_forward_noalloc is limited to " +
+                                               std::to_string((size_t)NUFFT_NOALLOC_SCRATCH_BYTES));
+    void* base = nullptr;
+    if ((st = noalloc_scratch(&base))) return st;
+    unsigned char* b = (unsigned char*)base;
+    cudaStream_t s = (cudaStream_t)stream;
+    // tables, computed in FP64 on the host and copied into the scratch array
+    for (int d = 0; d < p.D; ++d) {
+        std::vector<float> dp(p.N[d]);
+        for (int64_t n = 0; n < p.N[d]; ++n)
+            dp[n] = (float)(1.0 / kb_ft((double)(n - p.N[d] / 2) / (double)p.K[d], p.J, p.beta));
+        const int L = (int)p.K[d];
+        std::vector<float2> tw(L);
+        for (int t = 0; t < L; ++t) {
+            const double ang = -2.0 * M_PI * (double)t / (double)L;
+            tw[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+        p.d_deap[d] = (float*)(b + o_deap[d]);
+        p.d_tw[d] = (float2*)(b + o_tw[d]);
+        NJ_CUDA(cudaMemcpyAsync(p.d_deap[d], dp.data(), dp.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        NJ_CUDA(cudaMemcpyAsync(p.d_tw[d], tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+        build_fft_axis(L, p.axis[d]);
+        p.axis[d].tw = p.d_tw[d];
+    }
+    p.d_count = (int*)(b + o_count);
+    p.d_offsets = (int*)(b + o_offsets);
+    p.d_subp_off = (int*)(b + o_subp_off);
+    p.d_nsubp = (int*)(b + o_nsubp);
+    p.d_subp = (int4*)(b + o_subp);
+    p.d_local = (int*)(b + o_local);
+    p.d_binid = (int*)(b + o_binid);
+    p.d_pidx = (int4*)(b + o_pidx);
+    p.d_pfrac = (float4*)(b + o_pfrac);
+    p.d_G = (float2*)(b + o_G);
+    p.d_T = (float2*)(b + o_T);
+    p.G_elems = G;
+    p.T_elems = T;
+    p.M_cap = mc;   // capacity is the scratch slice: the sort never reallocates
+    // the bin sort zeroes its own counters; every workspace element is written before it is read
+    if ((st = do_set_points(&p, m, omega, s))) return st;
+    if (m == 0) return NUFFT_OK;
+    if ((st = forward_grids(&p, C, 1, 1, (const float2*)x, (const float2*)smaps, s))) return st;
+    GatherArgs g = gather_args(&p, C, 1, 1);
+    g.y = (float2*)y;
+    const int cpl = (C + g.G - 1) / g.G;
+    return launch(&p, PK_GATHER_FWD, s, [&] { return launch_gather(GM_FWD, g, cpl, s); });
+}
