@@ -8,6 +8,7 @@ namespace nj {
 constexpr int kMaxDim = 3;
 constexpr int kMaxStages = 12;
 constexpr int kKbTerms = 32;   // Horner terms of the Kaiser-Bessel power series
+constexpr int kJMin = 4;       // smallest interpolation width
 constexpr int kJMax = 8;       // largest interpolation width
 constexpr int kFftEpt = 16;    // complex elements held per thread in an FFT pass
 

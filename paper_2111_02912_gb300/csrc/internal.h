@@ -8,29 +8,79 @@
 namespace nj {
 
 // ---------------------------------------------------------------- sorting
+// Points are ordered by key = bin * cpb + cell, where the bin (a tile of B_d
+// cells per axis) and the cell inside it are those of the window start, so
+// each bin is a contiguous range sorted by cell.  cpb = prod B_d.
+constexpr int kScanPerBlock = 4096;   // keys scanned by one block of the key scan
+constexpr int kNbrStride = 64;        // ints per tile in tile_nbr: n, then 27 (start, prefix) pairs, total
+
 struct SortArgs {
     const float* omega;   // [D][M]
     int64_t m;
     int D, J;
     int K[kMaxDim];
     int B[kMaxDim], nb[kMaxDim];
-    int nbins, P;
+    int nbins, cpb, P;    // P: spread candidates per work item
+    int64_t nkeys;        // nbins * cpb
     float c_hi[kMaxDim], c_lo[kMaxDim];  // K/(2 pi) as a float pair
-    int* count;       // [nbins]
-    int* local;       // [M]
-    int* binid;       // [M]
-    int* offsets;     // [nbins + 1]
-    int* subp_off;    // [nbins + 1]
-    int4* subp;       // [nbins + M/P + 1]
-    int* nsubp;       // [1]
+    int* kcount;      // [nkeys]      points per key, then (in place) first sorted position of each key
+    int* bsum;        // [nkeys / kScanPerBlock + 1]
+    int* local;       // [M]          rank among the points of the same key
+    int* keyid;       // [M]
+    int* offsets;     // [nbins + 1]  first sorted point of each bin
+    int* item_off;    // [nbins + 1]  first spread work item of each tile
+    int* tile_parts;  // [nbins]      spread work items of each tile
+    int* tile_nbr;    // [nbins][kNbrStride]  bins that reach the tile: count, then (start, prefix) pairs
+    int4* items;      // [max_items]  {tile, part, nparts, 0}
+    int* nitems;      // [1]
     int4* pidx;       // [M]
     float4* pfrac;    // [M]
 };
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
-cudaError_t launch_bin_count(const SortArgs& a, cudaStream_t s);
-cudaError_t launch_bin_scan(const SortArgs& a, cudaStream_t s);
+cudaError_t launch_key_count(const SortArgs& a, cudaStream_t s);
+cudaError_t launch_key_scan(const SortArgs& a, cudaStream_t s);       // three kernels
+cudaError_t launch_tile_scan(const SortArgs& a, cudaStream_t s);
 cudaError_t launch_bin_scatter(const SortArgs& a, cudaStream_t s);
-cudaError_t launch_bin_subprob(const SortArgs& a, cudaStream_t s);
+cudaError_t launch_bin_items(const SortArgs& a, cudaStream_t s);
+
+// Bins whose points can reach tile `bin` (tiles are the bins).  A window
+// covers J cells to the right of its start, so along each axis these are the
+// tile's own bin and the bins holding the J-1 cells before its first cell
+// (periodic; at most three, without repeats).  Returns their linear ids.
+__device__ __forceinline__ int neighbour_bins(int D, const int* nb, const int* B, const int* K, int J, int bin,
+                                              int* out) {
+    int bc[kMaxDim] = {0, 0, 0};
+    int r = bin;
+    for (int d = D - 1; d >= 0; --d) {
+        bc[d] = r % nb[d];
+        r /= nb[d];
+    }
+    int lists[kMaxDim][3], len[kMaxDim] = {1, 1, 1};
+    for (int d = 0; d < kMaxDim; ++d) lists[d][0] = 0;
+    for (int d = 0; d < D; ++d) {
+        const int org = bc[d] * B[d];
+        int c1 = org - 1, c2 = org - (J - 1);
+        if (c1 < 0) c1 += K[d];
+        if (c2 < 0) c2 += K[d];
+        const int cand[3] = {bc[d], c1 / B[d], c2 / B[d]};
+        len[d] = 0;
+        for (int o = 0; o < 3; ++o) {
+            bool seen = false;
+            for (int q = 0; q < len[d]; ++q) seen |= lists[d][q] == cand[o];
+            if (!seen) lists[d][len[d]++] = cand[o];
+        }
+    }
+    int n = 0;
+    for (int i0 = 0; i0 < len[0]; ++i0)
+        for (int i1 = 0; i1 < len[1]; ++i1)
+            for (int i2 = 0; i2 < len[2]; ++i2) {
+                int id = lists[0][i0];
+                if (D > 1) id = id * nb[1] + lists[1][i1];
+                if (D > 2) id = id * nb[2] + lists[2][i2];
+                out[n++] = id;
+            }
+    return n;
+}
 
 // -------------------------------------------------------------------- FFT
 struct ImageSide {
@@ -79,23 +129,38 @@ struct GatherArgs {
     const float2* v;      // [C][M]
     float* grad;          // [D][M]
 };
-cudaError_t launch_gather(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);
+cudaError_t launch_gather_d1(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);
+cudaError_t launch_gather_d2(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);
+cudaError_t launch_gather_d3(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);
+inline cudaError_t launch_gather(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s) {
+    return a.D == 1 ? launch_gather_d1(mode, a, cpl, s)
+                    : (a.D == 2 ? launch_gather_d2(mode, a, cpl, s) : launch_gather_d3(mode, a, cpl, s));
+}
 
 struct SpreadArgs {
     PointsView pts;
     int D, J;
     int K[kMaxDim];
-    int B[kMaxDim], nb[kMaxDim], T[kMaxDim];   // bin edge, bins per dim, tile extent B+J-1
-    const int4* subp;
-    const int* nsubp;
-    int max_subp;
+    int B[kMaxDim], nb[kMaxDim];   // tile (= bin) edge, tiles per dim
+    int nbins;
+    const int* offsets;   // [nbins + 1]
+    const int* tile_nbr;  // [nbins][kNbrStride]
+    const int4* items;    // spread work items {tile, part, nparts, candidates}
+    const int* nitems;
+    const int* tile_parts;
+    int max_items, P;
     const float2* y;      // [C][M]
     int64_t M;
     int C, CC;            // coils, coils per block
-    int G, lgG;
+    int G, lgG;           // tap slots per warp (lanes = G slots x 32/G coils)
     KbPoly kb;
     float2* grid;         // [K...][C]
 };
 cudaError_t launch_spread(const SpreadArgs& a, int cpl, cudaStream_t s, size_t smem);
+cudaError_t launch_zero_heavy_tiles(const SpreadArgs& a, cudaStream_t s);
+int spread_min_slots(int D, int J);   // fewest tap slots per warp the spread kernel supports
+// Cell-owner spread: D in {2, 3}, every tile edge <= K - J + 1 and >= J - 1, prod B <= 512,
+// a.CC = coils per block (4, 8 or 16), a.P candidates per work item (<= prod B).
+cudaError_t launch_spread_cells(const SpreadArgs& a, cudaStream_t s);
 
 }  // namespace nj

@@ -7,6 +7,13 @@
 // product omega * c_hi, Dekker / Ogita-Rump-Oishi error-free product), so the
 // integer window start and the fractional offset keep ~2^-40 relative accuracy
 // of the FP64 value although all arithmetic is FP32.
+//
+// Counting sort by key = (bin, cell of the window start): bins are tiles of
+// B_d cells per axis; inside a bin, points are ordered by the cell their
+// window starts in, so points that share a window are adjacent.  The spread
+// (the adjoint interpolation) is output-driven: tile t owns its cells and
+// takes contributions from the points of the bins that can reach it, so the
+// sort also lists the spread's work items (candidate ranges of <= P points).
 #include <algorithm>
 
 #include "internal.h"
@@ -31,14 +38,16 @@ __device__ __forceinline__ void window_of(float w, float c_hi, float c_lo, int K
     k0 = (int)s;
 }
 
-__device__ __forceinline__ void point_record(const SortArgs& a, int64_t i, int4& ix, float4& fr, int& bin) {
+__device__ __forceinline__ void point_record(const SortArgs& a, int64_t i, int4& ix, float4& fr, int64_t& key) {
     int k0[3] = {0, 0, 0};
     float u0[3] = {0.f, 0.f, 0.f};
-    bin = 0;
+    int64_t bin = 0, cell = 0;
     for (int d = 0; d < a.D; ++d) {
         window_of(a.omega[(int64_t)d * a.m + i], a.c_hi[d], a.c_lo[d], a.K[d], a.J, k0[d], u0[d]);
         bin = bin * a.nb[d] + k0[d] / a.B[d];
+        cell = cell * a.B[d] + k0[d] % a.B[d];
     }
+    key = bin * a.cpb + cell;
     ix = make_int4(k0[0], k0[1], k0[2], (int)i);
     fr = make_float4(u0[0], u0[1], u0[2], 0.f);
 }
@@ -50,54 +59,125 @@ __global__ void k_zero(float4* p, int64_t n4, int* tail, int64_t ntail) {
     if (blockIdx.x == 0 && threadIdx.x < ntail) tail[threadIdx.x] = 0;
 }
 
-__global__ void k_bin_count(SortArgs a) {
+__global__ void k_key_count(SortArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.m) return;
     int4 ix;
     float4 fr;
-    int bin;
-    point_record(a, i, ix, fr, bin);
-    a.binid[i] = bin;
-    a.local[i] = atomicAdd(&a.count[bin], 1);
+    int64_t key;
+    point_record(a, i, ix, fr, key);
+    a.keyid[i] = (int)key;
+    a.local[i] = atomicAdd(&a.kcount[key], 1);
 }
 
-// One block: exclusive scans of the bin counts and of the per-bin numbers of
-// sub-problems (ceil(count / P)).
-__global__ void k_bin_scan(SortArgs a) {
-    __shared__ int s_pts[1024];
-    __shared__ int s_sub[1024];
-    const int t = threadIdx.x, nt = blockDim.x;
-    const int per = (a.nbins + nt - 1) / nt;
-    const int lo = min(a.nbins, t * per), hi = min(a.nbins, lo + per);
-    int sp = 0, ss = 0;
-    for (int b = lo; b < hi; ++b) {
-        const int c = a.count[b];
-        sp += c;
-        ss += (c + a.P - 1) / a.P;
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& excl) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
-    s_pts[t] = sp;
-    s_sub[t] = ss;
+    if (lane == 31) sh[wid] = x;
     __syncthreads();
-    for (int off = 1; off < nt; off <<= 1) {   // Hillis-Steele inclusive scan
-        int vp = 0, vs = 0;
-        if (t >= off) { vp = s_pts[t - off]; vs = s_sub[t - off]; }
-        __syncthreads();
-        s_pts[t] += vp;
-        s_sub[t] += vs;
-        __syncthreads();
+    if (wid == 0) {
+        int w = lane < nw ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) sh[lane] = w;
     }
-    int rp = t ? s_pts[t - 1] : 0, rs = t ? s_sub[t - 1] : 0;
+    __syncthreads();
+    const int total = sh[nw - 1];
+    excl = x - v + (wid ? sh[wid - 1] : 0);
+    __syncthreads();
+    return total;
+}
+
+// Pass 1: each block scans kScanPerBlock keys in place (exclusive, block-local).
+__global__ void __launch_bounds__(1024) k_scan_local(SortArgs a) {
+    __shared__ int sh[32];
+    constexpr int per = kScanPerBlock / 1024;
+    const int64_t base = (int64_t)blockIdx.x * kScanPerBlock + (int64_t)threadIdx.x * per;
+    int v[per], s = 0;
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+        v[q] = base + q < a.nkeys ? a.kcount[base + q] : 0;
+        s += v[q];
+    }
+    int excl;
+    const int total = block_exclusive_scan(s, sh, excl);
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+        if (base + q < a.nkeys) a.kcount[base + q] = excl;
+        excl += v[q];
+    }
+    if (threadIdx.x == 0) a.bsum[blockIdx.x] = total;
+}
+
+// Pass 2 (one block): exclusive scan of the block totals.
+__global__ void __launch_bounds__(1024) k_scan_bsum(SortArgs a, int nblk) {
+    __shared__ int sh[32];
+    const int per = (nblk + 1023) / 1024;
+    const int lo = min(nblk, (int)threadIdx.x * per), hi = min(nblk, lo + per);
+    int s = 0;
+    for (int b = lo; b < hi; ++b) s += a.bsum[b];
+    int excl;
+    block_exclusive_scan(s, sh, excl);
     for (int b = lo; b < hi; ++b) {
-        const int c = a.count[b];
-        a.offsets[b] = rp;
-        a.subp_off[b] = rs;
-        rp += c;
-        rs += (c + a.P - 1) / a.P;
+        const int v = a.bsum[b];
+        a.bsum[b] = excl;
+        excl += v;
     }
-    if (t == nt - 1) {
-        a.offsets[a.nbins] = s_pts[t];
-        a.subp_off[a.nbins] = s_sub[t];
-        a.nsubp[0] = s_sub[t];
+}
+
+// Pass 3: add the block offsets; record the first position of every bin.
+__global__ void k_scan_add(SortArgs a) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.nkeys) return;
+    const int v = a.kcount[k] + a.bsum[k / kScanPerBlock];
+    a.kcount[k] = v;
+    if (k % a.cpb == 0) a.offsets[k / a.cpb] = v;
+    if (k == a.nkeys - 1) a.offsets[a.nbins] = (int)a.m;
+}
+
+// One block: spread work items per tile (candidates = points of the bins that
+// can reach the tile, at most 3^D bins), and their exclusive scan.
+__global__ void __launch_bounds__(1024) k_tile_scan(SortArgs a) {
+    __shared__ int sh[32];
+    const int per = (a.nbins + 1023) / 1024;
+    const int lo = min(a.nbins, (int)threadIdx.x * per), hi = min(a.nbins, lo + per);
+    int nbr[27];
+    int si = 0;
+    for (int b = lo; b < hi; ++b) {
+        const int nn = neighbour_bins(a.D, a.nb, a.B, a.K, a.J, b, nbr);
+        int* tn = a.tile_nbr + (int64_t)b * kNbrStride;
+        tn[0] = nn;
+        int cand = 0;
+        for (int q = 0; q < nn; ++q) {
+            const int st = a.offsets[nbr[q]];
+            tn[1 + 2 * q] = st;
+            tn[2 + 2 * q] = cand;
+            cand += a.offsets[nbr[q] + 1] - st;
+        }
+        tn[1 + 2 * nn] = 0;
+        tn[2 + 2 * nn] = cand;
+        const int parts = max(1, (cand + a.P - 1) / a.P);
+        a.tile_parts[b] = parts;
+        si += parts;
+    }
+    int excl;
+    const int total = block_exclusive_scan(si, sh, excl);
+    for (int b = lo; b < hi; ++b) {
+        a.item_off[b] = excl;
+        excl += a.tile_parts[b];
+    }
+    if (threadIdx.x == 0) {
+        a.item_off[a.nbins] = total;
+        a.nitems[0] = total;
     }
 }
 
@@ -106,20 +186,18 @@ __global__ void k_bin_scatter(SortArgs a) {
     if (i >= a.m) return;
     int4 ix;
     float4 fr;
-    int bin;
-    point_record(a, i, ix, fr, bin);
-    const int dst = a.offsets[a.binid[i]] + a.local[i];
+    int64_t key;
+    point_record(a, i, ix, fr, key);
+    const int dst = a.kcount[a.keyid[i]] + a.local[i];
     a.pidx[dst] = ix;
     a.pfrac[dst] = fr;
 }
 
-__global__ void k_bin_subprob(SortArgs a) {
+__global__ void k_bin_items(SortArgs a) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= a.nbins) return;
-    const int start = a.offsets[b], cnt = a.offsets[b + 1] - start;
-    const int base = a.subp_off[b];
-    for (int s = 0; s * a.P < cnt; ++s)
-        a.subp[base + s] = make_int4(b, start + s * a.P, min(a.P, cnt - s * a.P), 0);
+    const int parts = a.tile_parts[b], base = a.item_off[b];
+    for (int k = 0; k < parts; ++k) a.items[base + k] = make_int4(b, k, parts, 0);
 }
 
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s) {
@@ -130,13 +208,20 @@ cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s) {
     k_zero<<<blocks, 256, 0, s>>>((float4*)p, n4, (int*)((char*)p + n4 * 16), ntail);
     return cudaGetLastError();
 }
-cudaError_t launch_bin_count(const SortArgs& a, cudaStream_t s) {
+cudaError_t launch_key_count(const SortArgs& a, cudaStream_t s) {
     if (a.m == 0) return cudaSuccess;
-    k_bin_count<<<(unsigned)((a.m + 255) / 256), 256, 0, s>>>(a);
+    k_key_count<<<(unsigned)((a.m + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_bin_scan(const SortArgs& a, cudaStream_t s) {
-    k_bin_scan<<<1, 1024, 0, s>>>(a);
+cudaError_t launch_key_scan(const SortArgs& a, cudaStream_t s) {
+    const int nblk = (int)((a.nkeys + kScanPerBlock - 1) / kScanPerBlock);
+    k_scan_local<<<nblk, 1024, 0, s>>>(a);
+    k_scan_bsum<<<1, 1024, 0, s>>>(a, nblk);
+    k_scan_add<<<(unsigned)((a.nkeys + 255) / 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_tile_scan(const SortArgs& a, cudaStream_t s) {
+    k_tile_scan<<<1, 1024, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_bin_scatter(const SortArgs& a, cudaStream_t s) {
@@ -144,8 +229,8 @@ cudaError_t launch_bin_scatter(const SortArgs& a, cudaStream_t s) {
     k_bin_scatter<<<(unsigned)((a.m + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_bin_subprob(const SortArgs& a, cudaStream_t s) {
-    k_bin_subprob<<<(a.nbins + 255) / 256, 256, 0, s>>>(a);
+cudaError_t launch_bin_items(const SortArgs& a, cudaStream_t s) {
+    k_bin_items<<<(a.nbins + 255) / 256, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,559 @@
+// Adjoint interpolation (spread), Sec. II-D: G[k] = sum_i psi(t_i - k) y_i, the
+// transpose of the gather, onto the oversampled grid [K...][C].
+//
+// Output-driven tiles.  The grid is cut into tiles (the bins of the sort); a
+// work item owns one tile and visits the points of the bins that can reach
+// it: its own bin and the bins holding the J-1 cells before it (a window
+// covers J cells to the right of its start).  A tile with few candidates is
+// one work item and is stored with plain coalesced writes, zeros included, so
+// the grid needs no clearing and no global atomics.  A tile with many
+// candidates (the k-space centre of radial trajectories) is split over several
+// work items; it is cleared first and each item adds its partial tile with
+// float2 vector atomics, skipping cells it did not touch.
+//
+// Inside a work item the warps take batches of 32 consecutive candidates in
+// turn and stage them one per lane (record, window test, the J*D kernel
+// weights and the y values go to shared memory).  It then walks the staged
+// candidates in order with its 32 lanes split into NS row slots x (32 / NS)
+// coils: lane (s, c) owns the window rows s, s + NS, ... for coil c, so no
+// two lanes of a warp ever address the same tile cell.  Points are sorted by
+// window start, so consecutive points that share a window (dense sampling
+// near the k-space centre) are summed in registers and added to the shared
+// tile once per run.
+#include "interp.cuh"
+
+namespace nj {
+
+template <int D, int J>
+struct SpreadShape {
+    // A window is JO outer rows (all axes but the last) of JI taps (the last axis);
+    // 1-D windows are J rows of one tap.
+    static constexpr int JO = D == 1 ? J : (D == 2 ? J : J * J);
+    static constexpr int JI = D == 1 ? 1 : J;
+    static constexpr int NT_CAP = 18;   // accumulators per lane
+    static constexpr int ns_for(int n) { return n >= 32 ? 32 : (((JO + n - 1) / n) * JI <= NT_CAP ? n : ns_for(2 * n)); }
+    static constexpr int NS_MIN = ns_for(1);          // fewest row slots keeping NR * JI <= NT_CAP
+    static constexpr int NR = (JO + NS_MIN - 1) / NS_MIN;
+};
+
+constexpr int kSpreadWarps = 8;
+constexpr int kSpreadCoilsPerWarp = 16;   // y staging per warp: 32 candidates x up to 16 coils
+
+template <int D, int J>
+__global__ void __launch_bounds__(256, 2) k_spread(SpreadArgs a) {
+    using SH = SpreadShape<D, J>;
+    constexpr int JO = SH::JO, JI = SH::JI, NR = SH::NR;
+    extern __shared__ float4 smem4[];
+    __shared__ float coef[kKbTerms];
+    __shared__ int s_start[27], s_pref[28], s_nn;
+    __shared__ float s_w[kSpreadWarps][32][D * J + 1];                 // kernel weights per staged candidate
+    __shared__ int4 s_ix[kSpreadWarps][32];                            // window start, original index
+    __shared__ float2 s_y[kSpreadWarps][32][kSpreadCoilsPerWarp + 1];  // y of the staged candidates
+    const int it = blockIdx.x;
+    if (it >= a.nitems[0]) return;     // block-uniform
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int4 item = a.items[it];
+    const int tile = item.x, part = item.y, nparts = item.z;
+    int nb[kMaxDim] = {a.nb[0], a.nb[1], a.nb[2]};
+    int org[kMaxDim] = {0, 0, 0}, Bt[kMaxDim] = {1, 1, 1}, Kd[kMaxDim] = {1, 1, 1};
+    {
+        int r = tile;
+        for (int d = D - 1; d >= 0; --d) {
+            const int bc = r % nb[d];
+            r /= nb[d];
+            Kd[d] = a.K[d];
+            org[d] = bc * a.B[d];
+            Bt[d] = min(a.B[d], Kd[d] - org[d]);
+        }
+    }
+    const int c0 = blockIdx.y * a.CC;
+    const int ncc = min(a.CC, a.C - c0);
+    const int CC = a.CC;
+    const int tcells = Bt[0] * Bt[1] * Bt[2];
+    float2* tl = (float2*)smem4;   // [tcells][CC]
+
+    if (tid < kKbTerms) coef[tid] = a.kb.a[tid];
+    {   // bins that reach this tile (listed by the sort)
+        const int* tn = a.tile_nbr + (int64_t)tile * kNbrStride;
+        if (tid == 0) s_nn = tn[0];
+        if (tid < 27) s_start[tid] = tn[1 + 2 * tid];      // entries past the count are never used
+        if (tid < 28) s_pref[tid] = tn[2 + 2 * tid];
+    }
+    {   // clear the tile
+        float4* t4 = (float4*)tl;
+        const int n4 = tcells * CC / 2;
+        for (int i = tid; i < n4; i += blockDim.x) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((tcells * CC) & 1 && tid == 0) tl[tcells * CC - 1] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+
+    // lane roles: NS row slots x CCW coils; slot s owns rows s, s + NS, ...
+    const int NS = a.G;
+    const int CCW = 32 / NS;
+    const int slot = lane / CCW, cw = lane - slot * CCW;
+    const int nn = s_nn;
+    const int lo = part * a.P, hi = min(s_pref[nn], lo + a.P);
+    const float two_over_j = a.kb.two_over_j;
+    int q = 0;   // neighbour-bin cursor of this lane's staged candidate
+
+    for (int cp = 0; cp < ncc; cp += CCW) {
+        const int c = cp + cw;
+        const bool cok = c < ncc;
+        const int nyc = min(CCW, ncc - cp);   // coils staged per candidate in this pass
+        float2 acc[NR][JI];
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+#pragma unroll
+            for (int j = 0; j < JI; ++j) acc[r][j] = make_float2(0.f, 0.f);
+        int rk0 = -1, rk1 = 0, rk2 = 0;   // window start of the open run (rk0 < 0: none)
+        bool run_in = false;             // the open run's window lies wholly inside the tile
+
+        auto flush = [&]() {
+            if (rk0 < 0) return;
+            if (cok) {
+                int ls[kMaxDim] = {rk0 - org[0], rk1 - org[1], rk2 - org[2]};
+#pragma unroll
+                for (int d = 0; d < D; ++d)
+                    if (ls[d] < 0) ls[d] += Kd[d];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const int o = slot + NS * r;   // outer row: (j0) in 2-D, (j0, j1) in 3-D, tap in 1-D
+                    if (o >= JO) continue;
+                    int rowcell;
+                    bool rin = true;
+                    if (D == 1) {
+                        int l = ls[0] + o;
+                        if (l >= Kd[0]) l -= Kd[0];
+                        rin = l < Bt[0];
+                        rowcell = l;
+                    } else if (D == 2) {
+                        int l = ls[0] + o;
+                        if (l >= Kd[0]) l -= Kd[0];
+                        rin = l < Bt[0];
+                        rowcell = l * Bt[1];
+                    } else {
+                        int l0 = ls[0] + o / J, l1 = ls[1] + o % J;
+                        if (l0 >= Kd[0]) l0 -= Kd[0];
+                        if (l1 >= Kd[1]) l1 -= Kd[1];
+                        rin = l0 < Bt[0] && l1 < Bt[1];
+                        rowcell = (l0 * Bt[1] + l1) * Bt[2];
+                    }
+                    if (!rin) continue;
+                    const int li0 = D == 1 ? 0 : ls[D - 1];
+                    const int Kl = Kd[D - 1], Bl = Bt[D - 1];
+#pragma unroll
+                    for (int j = 0; j < JI; ++j) {
+                        if (acc[r][j].x == 0.f && acc[r][j].y == 0.f) continue;
+                        int l = li0 + j;
+                        if (D > 1 && !run_in) {
+                            if (l >= Kl) l -= Kl;
+                            if (l >= Bl) continue;
+                        }
+                        float2* tp = tl + (size_t)(rowcell + (D > 1 ? l : 0)) * CC + c;
+                        atomicAdd(&tp->x, acc[r][j].x);
+                        atomicAdd(&tp->y, acc[r][j].y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+#pragma unroll
+                for (int j = 0; j < JI; ++j) acc[r][j] = make_float2(0.f, 0.f);
+            rk0 = -1;
+        };
+
+        q = 0;
+        // batches of 32 consecutive candidates, dealt to the warps in turn
+        for (int bb = lo + 32 * warp; bb < hi; bb += 32 * kSpreadWarps) {
+            // stage 32 candidates, one per lane: record, hit test, weights, y
+            const int cand = bb + lane;
+            bool hit = false, inside = false;
+            if (cand < hi) {
+                while (q + 1 < nn && s_pref[q + 1] <= cand) ++q;
+                const int64_t p = s_start[q] + (cand - s_pref[q]);
+                const int4 ix = a.pts.idx[p];
+                hit = true;
+                inside = true;
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    int ls = (d == 0 ? ix.x : (d == 1 ? ix.y : ix.z)) - org[d];
+                    if (ls < 0) ls += Kd[d];
+                    const int lend = ls + J - 1;   // last tap, unwrapped
+                    hit = hit && (ls < Bt[d] || lend >= Kd[d]);
+                    inside = inside && lend < Bt[d];
+                }
+                if (hit) {
+                    const float4 fr = a.pts.frac[p];
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        const float u0 = d == 0 ? fr.x : (d == 1 ? fr.y : fr.z);
+#pragma unroll
+                        for (int j = 0; j < J; ++j) s_w[warp][lane][d * J + j] = kb_psi(coef, two_over_j, u0 - (float)j);
+                    }
+                    for (int cc = 0; cc < nyc; ++cc)
+                        s_y[warp][lane][cc] = __ldg(a.y + (int64_t)(c0 + cp + cc) * a.M + ix.w);
+                    s_ix[warp][lane] = make_int4(ix.x, ix.y, ix.z, inside ? 1 : 0);
+                }
+            }
+            unsigned hits = __ballot_sync(0xffffffffu, hit);
+            __syncwarp();
+            while (hits) {
+                const int b = __ffs(hits) - 1;
+                hits &= hits - 1;
+                const int4 rec = s_ix[warp][b];
+                if (rec.x != rk0 || (D > 1 && rec.y != rk1) || (D > 2 && rec.z != rk2)) {
+                    flush();
+                    rk0 = rec.x;
+                    rk1 = rec.y;
+                    rk2 = rec.z;
+                    run_in = rec.w != 0;
+                }
+                const float* wv = s_w[warp][b];
+                const float2 yv = cok ? s_y[warp][b][cw] : make_float2(0.f, 0.f);
+                float wi[JI];
+#pragma unroll
+                for (int j = 0; j < JI; ++j) wi[j] = D == 1 ? 1.f : wv[(D - 1) * J + j];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const int o = slot + NS * r;
+                    if (o >= JO) continue;
+                    const float wo = D == 3 ? wv[o / J] * wv[J + o % J] : wv[o];
+                    const float2 yw = make_float2(wo * yv.x, wo * yv.y);
+#pragma unroll
+                    for (int j = 0; j < JI; ++j) {
+                        acc[r][j].x = fmaf(wi[j], yw.x, acc[r][j].x);
+                        acc[r][j].y = fmaf(wi[j], yw.y, acc[r][j].y);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        flush();
+    }
+    __syncthreads();
+
+    // write the tile row by row: a row (all axes but the last fixed) is Bt_last cells,
+    // contiguous in the grid; element i of a row is cell i / ncc, coil i % ncc
+    const int K1 = D > 1 ? Kd[1] : 1, K2 = D > 2 ? Kd[2] : 1;
+    const int Bl = Bt[D - 1];
+    const int rowlen = Bl * ncc;
+    const int nrows = tcells / Bl;
+    const uint32_t mg = ncc > 1 ? (uint32_t)((((uint64_t)1 << 32) + ncc - 1) / ncc) : 0u;
+    for (int f = tid; f < nrows * rowlen; f += blockDim.x) {
+        const int row = f / rowlen, i = f - row * rowlen;   // rowlen: block-uniform
+        const int cell_in_row = (int)div_magic((uint32_t)i, (uint32_t)ncc, mg);
+        const int cl = i - cell_in_row * ncc;
+        int r0 = row, r1 = 0;
+        if (D == 3) { r1 = row % Bt[1]; r0 = row / Bt[1]; }
+        int64_t gcell;
+        if (D == 1) gcell = org[0] + cell_in_row;
+        else if (D == 2) gcell = (int64_t)(org[0] + r0) * K1 + org[1] + cell_in_row;
+        else gcell = ((int64_t)(org[0] + r0) * K1 + (org[1] + r1)) * K2 + org[2] + cell_in_row;
+        const float2 v = tl[(size_t)(row * Bl + cell_in_row) * CC + cl];
+        float2* dst = a.grid + gcell * a.C + c0 + cl;
+        if (nparts == 1) *dst = v;
+        else if (v.x != 0.f || v.y != 0.f) atomicAdd(dst, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Cell-owner spread (fast path).  Used when no window can cover a tile twice
+// (every tile edge Bt_d <= K_d - J + 1) and tiles are at least J - 1 wide.
+// The block stages the work item's candidates (one per thread), keeps those
+// whose window reaches the tile, and counting-sorts them in shared memory by
+// window start, in coordinates e_d = start_d - org_d + J - 1 in [0, Bt_d + J - 1).
+// Thread t then owns tile cell t for CPT coils: the points covering cell l are
+// those with e_d in [l_d, l_d + J - 1] for every axis, with tap j_d = l_d + J - 1 - e_d,
+// so it sums w * y over the J^D start cells around it in registers.  No
+// atomics on the tile; within a start cell the points are summed in the order
+// they were placed (rounding-level differences between runs).
+template <int D, int J, int CPT>
+__global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
+    extern __shared__ float4 smem4[];
+    __shared__ float coef[kKbTerms];
+    __shared__ int s_start[27], s_pref[28], s_nn, s_nh;
+    const int it = blockIdx.x;
+    if (it >= a.nitems[0]) return;     // block-uniform
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int4 item = a.items[it];
+    const int tile = item.x, part = item.y, nparts = item.z;
+    int org[kMaxDim] = {0, 0, 0}, Bt[kMaxDim] = {1, 1, 1}, Kd[kMaxDim] = {1, 1, 1}, E[kMaxDim] = {1, 1, 1};
+    {
+        int r = tile;
+        for (int d = D - 1; d >= 0; --d) {
+            const int nbd = a.nb[d];
+            const int bc = r % nbd;
+            r /= nbd;
+            Kd[d] = a.K[d];
+            org[d] = bc * a.B[d];
+            Bt[d] = min(a.B[d], Kd[d] - org[d]);
+            E[d] = Bt[d] + J - 1;
+        }
+    }
+    const int NE = E[0] * E[1] * E[2];     // start-cell bins of this tile
+    const int P = a.P;
+    const int c0 = blockIdx.y * CPT;
+    const int ncc = min(CPT, a.C - c0);
+    // shared layout: weights [P][D*J], y [P][CPT+1], bin of each hit [P], sorted hits [P], counts [NE+1]
+    float* s_w = (float*)smem4;
+    float2* s_y = (float2*)(s_w + P * D * J + ((P * D * J) & 1));
+    int* s_e = (int*)(s_y + (size_t)P * (CPT + 1));
+    int* s_list = s_e + P;
+    int* s_cnt = s_list + P;
+
+    if (tid < kKbTerms) coef[tid] = a.kb.a[tid];
+    {
+        const int* tn = a.tile_nbr + (int64_t)tile * kNbrStride;
+        if (tid == 0) { s_nn = tn[0]; s_nh = 0; }
+        if (tid < 27) s_start[tid] = tn[1 + 2 * tid];      // entries past the count are never used
+        if (tid < 28) s_pref[tid] = tn[2 + 2 * tid];
+    }
+    for (int i = tid; i <= NE; i += nt) s_cnt[i] = 0;
+    __syncthreads();
+
+    // stage: thread t takes candidate lo + t
+    const int nn = s_nn;
+    const int lo = part * P, hi = min(s_pref[nn], lo + P);
+    const int cand = lo + tid;
+    int my_e = -1;
+    int my_slot = -1;
+    if (tid < P && cand < hi) {
+        int q = 0;
+        while (q + 1 < nn && s_pref[q + 1] <= cand) ++q;
+        const int64_t p = s_start[q] + (cand - s_pref[q]);
+        const int4 ix = a.pts.idx[p];
+        bool hit = true;
+        int e = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            int sd = (d == 0 ? ix.x : (d == 1 ? ix.y : ix.z)) - org[d];
+            if (sd < 0) sd += Kd[d];
+            if (sd > Kd[d] - J) sd -= Kd[d];           // starts up to J-1 cells before the tile
+            hit = hit && sd >= -(J - 1) && sd < Bt[d];
+            e = e * E[d] + (sd + J - 1);
+        }
+        if (hit) {
+            my_slot = atomicAdd(&s_nh, 1);
+            my_e = e;
+            const float4 fr = a.pts.frac[p];
+            float* w = s_w + my_slot * (D * J);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const float u0 = d == 0 ? fr.x : (d == 1 ? fr.y : fr.z);
+#pragma unroll
+                for (int j = 0; j < J; ++j) w[d * J + j] = kb_psi(coef, a.kb.two_over_j, u0 - (float)j);
+            }
+            float2* yv = s_y + (size_t)my_slot * (CPT + 1);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c)
+                yv[c] = c < ncc ? __ldg(a.y + (int64_t)(c0 + c) * a.M + ix.w) : make_float2(0.f, 0.f);
+            s_e[my_slot] = e;
+            atomicAdd(&s_cnt[e], 1);
+        }
+    }
+    __syncthreads();
+    // exclusive scan of the bin counts (NE is at most a few thousand): each thread a chunk
+    {
+        __shared__ int s_part[512];
+        const int per = (NE + nt - 1) / nt;
+        const int b0 = min(NE, tid * per), b1 = min(NE, b0 + per);
+        int sum = 0;
+        for (int b = b0; b < b1; ++b) sum += s_cnt[b];
+        s_part[tid] = sum;
+        __syncthreads();
+        for (int off = 1; off < nt; off <<= 1) {
+            const int v = tid >= off ? s_part[tid - off] : 0;
+            __syncthreads();
+            s_part[tid] += v;
+            __syncthreads();
+        }
+        int run = tid ? s_part[tid - 1] : 0;
+        for (int b = b0; b < b1; ++b) {
+            const int c = s_cnt[b];
+            s_cnt[b] = run;
+            run += c;
+        }
+        if (tid == nt - 1) s_cnt[NE] = run;
+    }
+    __syncthreads();
+    // place hits: s_cnt[e] becomes the cursor of bin e (its end once all are placed)
+    if (my_slot >= 0) s_list[atomicAdd(&s_cnt[my_e], 1)] = my_slot;
+    __syncthreads();
+
+    // gather: thread t owns cell t (the block has one thread per tile cell)
+    const int tcells = Bt[0] * Bt[1] * Bt[2];
+    const int cell = tid;
+    float2 acc[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) acc[c] = make_float2(0.f, 0.f);
+    if (cell < tcells) {
+        int l[kMaxDim] = {0, 0, 0};
+        {
+            int r = cell;
+            for (int d = D - 1; d >= 0; --d) {
+                l[d] = r % Bt[d];
+                r /= Bt[d];
+            }
+        }
+        // loops kept rolled: one copy of the pair loop keeps the code small
+#pragma unroll 1
+        for (int a0 = 0; a0 < J; ++a0) {
+            const int e0 = l[0] + a0;            // tap j0 = J - 1 - a0
+#pragma unroll 1
+            for (int a1 = 0; a1 < (D > 1 ? J : 1); ++a1) {
+                const int e1 = D > 1 ? l[1] + a1 : 0;
+#pragma unroll 1
+                for (int a2 = 0; a2 < (D > 2 ? J : 1); ++a2) {
+                    const int e2 = D > 2 ? l[2] + a2 : 0;
+                    const int e = (e0 * E[1] + e1) * E[2] + e2;
+                    const int h0 = e ? s_cnt[e - 1] : 0, h1 = s_cnt[e];   // cursors now mark bin ends
+                    for (int hh = h0; hh < h1; ++hh) {
+                        const int h = s_list[hh];
+                        const float* w = s_w + h * (D * J);
+                        float wt = w[J - 1 - a0];
+                        if (D > 1) wt *= w[J + J - 1 - a1];
+                        if (D > 2) wt *= w[2 * J + J - 1 - a2];
+                        const float2* yv = s_y + (size_t)h * (CPT + 1);
+#pragma unroll
+                        for (int c = 0; c < CPT; ++c) {
+                            acc[c].x = fmaf(wt, yv[c].x, acc[c].x);
+                            acc[c].y = fmaf(wt, yv[c].y, acc[c].y);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();   // every staged y has been read
+    if (cell < tcells) {
+        float2* o = s_y + (size_t)cell * (CPT + 1);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) o[c] = acc[c];
+    }
+    __syncthreads();
+    // write the tile coil-fastest: a tile row is Bt_last cells, contiguous in the grid
+    const int K1 = D > 1 ? Kd[1] : 1, K2 = D > 2 ? Kd[2] : 1;
+    const int Bl = Bt[D - 1];
+    const int rowlen = Bl * ncc;
+    const int nrows = tcells / Bl;
+    const uint32_t mg = ncc > 1 ? (uint32_t)((((uint64_t)1 << 32) + ncc - 1) / ncc) : 0u;
+    for (int f = tid; f < nrows * rowlen; f += nt) {
+        const int row = f / rowlen, i = f - row * rowlen;
+        const int cr = (int)div_magic((uint32_t)i, (uint32_t)ncc, mg);
+        const int c = i - cr * ncc;
+        int r0 = row, r1 = 0;
+        if (D == 3) { r1 = row % Bt[1]; r0 = row / Bt[1]; }
+        const int64_t gcell = D == 2 ? (int64_t)(org[0] + r0) * K1 + org[1] + cr
+                                     : ((int64_t)(org[0] + r0) * K1 + (org[1] + r1)) * K2 + org[2] + cr;
+        const float2 v = s_y[(size_t)(row * Bl + cr) * (CPT + 1) + c];
+        float2* dst = a.grid + gcell * a.C + c0 + c;
+        if (nparts == 1) *dst = v;
+        else if (v.x != 0.f || v.y != 0.f) atomicAdd(dst, v);
+    }
+}
+
+template <int D, int J>
+static cudaError_t spread_cells_cpt(const SpreadArgs& a, cudaStream_t s, int threads) {
+    const int cpt = a.CC;
+    int E = 1;
+    for (int d = 0; d < D; ++d) E *= a.B[d] + J - 1;
+    const size_t smem = (size_t)a.P * D * J * sizeof(float) + sizeof(float) + (size_t)a.P * (cpt + 1) * sizeof(float2) +
+                        2 * (size_t)a.P * sizeof(int) + (size_t)(E + 1) * sizeof(int);
+    dim3 grid((unsigned)a.max_items, (unsigned)((a.C + cpt - 1) / cpt));
+    if (cpt <= 4) {
+        cudaFuncSetAttribute(k_spread_cells<D, J, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_spread_cells<D, J, 4><<<grid, threads, smem, s>>>(a);
+    } else if (cpt <= 8) {
+        cudaFuncSetAttribute(k_spread_cells<D, J, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_spread_cells<D, J, 8><<<grid, threads, smem, s>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_spread_cells<D, J, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_spread_cells<D, J, 16><<<grid, threads, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t spread_cells_d(const SpreadArgs& a, cudaStream_t s, int threads) {
+    switch (a.J) {
+        case 4: return spread_cells_cpt<D, 4>(a, s, threads);
+        case 5: return spread_cells_cpt<D, 5>(a, s, threads);
+        case 6: return spread_cells_cpt<D, 6>(a, s, threads);
+        case 7: return spread_cells_cpt<D, 7>(a, s, threads);
+        default: return spread_cells_cpt<D, 8>(a, s, threads);
+    }
+}
+
+cudaError_t launch_spread_cells(const SpreadArgs& a, cudaStream_t s) {
+    if (a.max_items == 0) return cudaSuccess;
+    int threads = 1;
+    for (int d = 0; d < a.D; ++d) threads *= a.B[d];
+    if (a.D == 2) return spread_cells_d<2>(a, s, threads);
+    return spread_cells_d<3>(a, s, threads);
+}
+
+// Clears the cells (all coils) of the tiles that are split over several work items.
+__global__ void k_zero_heavy_tiles(SpreadArgs a) {
+    const int tile = blockIdx.x;
+    if (a.tile_parts[tile] <= 1) return;
+    int r = tile, org[kMaxDim] = {0, 0, 0}, Bt[kMaxDim] = {1, 1, 1}, Kd[kMaxDim] = {1, 1, 1};
+    for (int d = a.D - 1; d >= 0; --d) {
+        const int bc = r % a.nb[d];
+        r /= a.nb[d];
+        Kd[d] = a.K[d];
+        org[d] = bc * a.B[d];
+        Bt[d] = min(a.B[d], Kd[d] - org[d]);
+    }
+    const int n = Bt[0] * Bt[1] * Bt[2] * a.C;
+    for (int f = threadIdx.x; f < n; f += blockDim.x) {
+        const int c = f % a.C, cell = f / a.C;
+        const int l2 = cell % Bt[2], q = cell / Bt[2];
+        const int l1 = q % Bt[1], l0 = q / Bt[1];
+        const int64_t gcell = ((int64_t)(org[0] + l0) * Kd[1] + (org[1] + l1)) * Kd[2] + (org[2] + l2);
+        a.grid[gcell * a.C + c] = make_float2(0.f, 0.f);
+    }
+}
+
+template <int D, int J>
+static cudaError_t spread_j(const SpreadArgs& a, cudaStream_t s, size_t smem, dim3 grid) {
+    cudaFuncSetAttribute(k_spread<D, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_spread<D, J><<<grid, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t spread_d(const SpreadArgs& a, cudaStream_t s, size_t smem, dim3 grid) {
+    switch (a.J) {
+        case 4: return spread_j<D, 4>(a, s, smem, grid);
+        case 5: return spread_j<D, 5>(a, s, smem, grid);
+        case 6: return spread_j<D, 6>(a, s, smem, grid);
+        case 7: return spread_j<D, 7>(a, s, smem, grid);
+        default: return spread_j<D, 8>(a, s, smem, grid);
+    }
+}
+
+int spread_min_slots(int D, int J) {
+    switch (D * 16 + J) {
+#define NJ_NS(DD, JJ) case DD * 16 + JJ: return SpreadShape<DD, JJ>::NS_MIN;
+        NJ_NS(1, 4) NJ_NS(1, 5) NJ_NS(1, 6) NJ_NS(1, 7) NJ_NS(1, 8)
+        NJ_NS(2, 4) NJ_NS(2, 5) NJ_NS(2, 6) NJ_NS(2, 7) NJ_NS(2, 8)
+        NJ_NS(3, 4) NJ_NS(3, 5) NJ_NS(3, 6) NJ_NS(3, 7) NJ_NS(3, 8)
+#undef NJ_NS
+        default: return 32;
+    }
+}
+
+cudaError_t launch_spread(const SpreadArgs& a, int /*cpl*/, cudaStream_t s, size_t smem) {
+    dim3 grid((unsigned)a.max_items, (unsigned)((a.C + a.CC - 1) / a.CC));
+    if (a.max_items == 0) return cudaSuccess;
+    if (a.D == 1) return spread_d<1>(a, s, smem, grid);
+    if (a.D == 2) return spread_d<2>(a, s, smem, grid);
+    return spread_d<3>(a, s, smem, grid);
+}
+
+cudaError_t launch_zero_heavy_tiles(const SpreadArgs& a, cudaStream_t s) {
+    k_zero_heavy_tiles<<<a.nbins, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace nj

@@ -35,12 +35,12 @@ int fail(int status, const std::string& msg) {
     } while (0)
 
 enum ProfKind {
-    PK_ZERO, PK_BIN_COUNT, PK_BIN_SCAN, PK_BIN_SCATTER, PK_BIN_SUBPROB, PK_FFT_FWD_FIRST, PK_FFT_FWD_MID,
-    PK_FFT_INV_MID, PK_FFT_INV_LAST, PK_GATHER_FWD, PK_GATHER_JVP, PK_GATHER_VJP, PK_SPREAD, PK_COUNT
+    PK_ZERO, PK_BIN_COUNT, PK_BIN_SCAN, PK_TILE_SCAN, PK_BIN_SCATTER, PK_BIN_ITEMS, PK_FFT_FWD_FIRST, PK_FFT_FWD_MID,
+    PK_FFT_INV_MID, PK_FFT_INV_LAST, PK_GATHER_FWD, PK_GATHER_JVP, PK_GATHER_VJP, PK_ZERO_HEAVY, PK_SPREAD, PK_COUNT
 };
-const char* kProfNames[PK_COUNT] = {"zero", "bin_count", "bin_scan", "bin_scatter", "bin_subprob", "fft_fwd_first",
+const char* kProfNames[PK_COUNT] = {"zero", "bin_count", "bin_scan", "tile_scan", "bin_scatter", "bin_items", "fft_fwd_first",
                                     "fft_fwd_mid", "fft_inv_mid", "fft_inv_last", "gather_fwd", "gather_jvp",
-                                    "gather_vjp", "spread"};
+                                    "gather_vjp", "zero_heavy", "spread"};
 
 int64_t grid_size(int64_t n, double sigma) {
     int64_t k = (int64_t)std::ceil(sigma * (double)n - 1e-9);
@@ -80,14 +80,19 @@ struct nufft_plan_s {
     float2* d_tw[3] = {nullptr, nullptr, nullptr};
     FftAxis axis[3]{};
     // bins
-    int B[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, T[3] = {1, 1, 1}, nbins = 1, P = 1024, CCmax = 1;
-    int* d_count = nullptr;
+    int B[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, nbins = 1, cpb = 1, P = 1024, CCmax = 1;
+    bool cell_spread = false;   // spread by the cell-owner kernel (else the general kernel)
+    int64_t nkeys = 1;
+    int* d_kcount = nullptr;
+    int* d_bsum = nullptr;
     int* d_offsets = nullptr;
-    int* d_subp_off = nullptr;
-    int* d_nsubp = nullptr;
-    int4* d_subp = nullptr;
+    int* d_item_off = nullptr;
+    int* d_tile_parts = nullptr;
+    int* d_tile_nbr = nullptr;
+    int* d_nitems = nullptr;
+    int4* d_items = nullptr;
     int* d_local = nullptr;
-    int* d_binid = nullptr;
+    int* d_keyid = nullptr;
     int4* d_pidx = nullptr;
     float4* d_pfrac = nullptr;
     float c_hi[3] = {0, 0, 0}, c_lo[3] = {0, 0, 0};
@@ -169,8 +174,8 @@ double kb_ft(double f, int J, double beta) {
 
 void free_plan(nufft_plan_s* p) {
     for (int d = 0; d < 3; ++d) { cudaFree(p->d_deap[d]); cudaFree(p->d_tw[d]); }
-    cudaFree(p->d_count); cudaFree(p->d_offsets); cudaFree(p->d_subp_off); cudaFree(p->d_nsubp);
-    cudaFree(p->d_subp); cudaFree(p->d_local); cudaFree(p->d_binid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
+    cudaFree(p->d_kcount); cudaFree(p->d_bsum); cudaFree(p->d_offsets); cudaFree(p->d_item_off); cudaFree(p->d_tile_parts); cudaFree(p->d_tile_nbr);
+    cudaFree(p->d_nitems); cudaFree(p->d_items); cudaFree(p->d_local); cudaFree(p->d_keyid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
     cudaFree(p->d_G); cudaFree(p->d_T);
     for (auto& e : p->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto e : p->pool) cudaEventDestroy(e);
@@ -184,7 +189,7 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
     p.sigma = o->sigma > 0 ? o->sigma : 2.0;
     if (p.sigma <= 1.0 || p.sigma > 4.0) return fail(NUFFT_ERR_UNSUPPORTED, "sigma must lie in (1, 4]");
     p.J = o->J ? o->J : 6;
-    if (p.J < 2 || p.J > kJMax) return fail(NUFFT_ERR_UNSUPPORTED, "J must lie in [2, 8]");
+    if (p.J < kJMin || p.J > kJMax) return fail(NUFFT_ERR_UNSUPPORTED, "J must lie in [4, 8]");
     p.maxC = o->max_coils ? o->max_coils : 1;
     if (p.maxC < 1 || p.maxC > 128) return fail(NUFFT_ERR_UNSUPPORTED, "max_coils must lie in [1, 128]");
     p.Nimg = 1;
@@ -201,25 +206,31 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
     }
     p.beta = o->beta > 0 ? o->beta
                          : M_PI * std::sqrt(std::pow(p.J / p.sigma, 2) * std::pow(p.sigma - 0.5, 2) - 0.8);
-    // bins: tile edge B_d, tile extent B_d + J - 1 per dim; coils per spread block
-    const int defB[3][3] = {{512, 1, 1}, {32, 32, 1}, {16, 16, 8}};
+    // bins = spread tiles of B_d cells per axis; coils per spread block from the tile size
+    const int defB[3][3] = {{256, 1, 1}, {16, 16, 1}, {8, 8, 8}};
     size_t tcells = 1;
     for (int d = 0; d < p.D; ++d) {
         int b = o->bin_size[d] > 0 ? o->bin_size[d] : defB[p.D - 1][d];
         b = (int)std::min<int64_t>(b, p.K[d]);
+        if (b < p.J) b = (int)std::min<int64_t>(p.J, p.K[d]);   // a window must not pass a whole tile
         p.B[d] = b;
         p.nb[d] = (int)((p.K[d] + b - 1) / b);
-        p.T[d] = b + p.J - 1;
-        tcells *= p.T[d];
+        tcells *= b;
     }
     p.nbins = 1;
     for (int d = 0; d < p.D; ++d) p.nbins *= p.nb[d];
-    const size_t tile_budget = 96 * 1024;
-    const size_t wbytes = (256 * p.D * kJMax) * sizeof(float);
-    if (tcells * sizeof(float2) + wbytes > tile_budget + 16 * 1024)
+    if (p.nbins > (1 << 24)) return fail(NUFFT_ERR_UNSUPPORTED, "too many bins; enlarge bin_size");
+    p.cpb = (int)tcells;
+    p.nkeys = (int64_t)p.nbins * p.cpb;
+    if (p.nkeys >= ((int64_t)1 << 31)) return fail(NUFFT_ERR_UNSUPPORTED, "grid too large for the point sort");
+    const size_t tile_budget = 32 * 1024;
+    if (tcells * sizeof(float2) > tile_budget)
         return fail(NUFFT_ERR_UNSUPPORTED, "spread tile does not fit in shared memory; reduce bin_size");
     p.CCmax = (int)std::max<size_t>(1, std::min<size_t>(32, tile_budget / (tcells * sizeof(float2))));
-    p.P = p.D == 3 ? 512 : 1024;
+    // spread path: cell-owner tiles when no window can cover a tile twice, else the general kernel
+    p.cell_spread = p.D >= 2 && tcells <= 512;
+    for (int d = 0; d < p.D; ++d) p.cell_spread = p.cell_spread && p.B[d] + p.J - 1 <= p.K[d];
+    p.P = p.cell_spread ? (int)tcells : (p.D == 3 ? 1024 : 512);
     // KB power-series coefficients a_k = (beta^2/4)^k / (k!)^2
     double ak = 1.0, sum = 0.0;
     const double q = p.beta * p.beta / 4.0;
@@ -262,19 +273,25 @@ void workspace_elems(const nufft_plan_s& p, size_t& G, size_t& T) {
     if (T == 0) T = 1;
 }
 
+// Upper bound of the spread work items: one per tile plus one per P candidates;
+// every point is a candidate of at most 3^D tiles.
+size_t max_items(const nufft_plan_s& p, int64_t cap) {
+    int nbr = 1;
+    for (int d = 0; d < p.D; ++d) nbr *= std::min(3, p.nb[d]);
+    return (size_t)p.nbins + (size_t)((nbr * cap + p.P - 1) / p.P) + 1;
+}
+
 size_t point_bytes(const nufft_plan_s& p, int64_t cap) {
-    const size_t nsub = (size_t)p.nbins + (size_t)(cap / p.P) + 1;
-    return (size_t)cap * (2 * sizeof(int) + sizeof(int4) + sizeof(float4)) + nsub * sizeof(int4);
+    return (size_t)cap * (2 * sizeof(int) + sizeof(int4) + sizeof(float4)) + max_items(p, cap) * sizeof(int4);
 }
 
 int alloc_points(nufft_plan_s* p, int64_t cap) {
-    cudaFree(p->d_subp); cudaFree(p->d_local); cudaFree(p->d_binid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
-    p->d_subp = nullptr; p->d_local = p->d_binid = nullptr; p->d_pidx = nullptr; p->d_pfrac = nullptr;
+    cudaFree(p->d_items); cudaFree(p->d_local); cudaFree(p->d_keyid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
+    p->d_items = nullptr; p->d_local = p->d_keyid = nullptr; p->d_pidx = nullptr; p->d_pfrac = nullptr;
     const size_t c = (size_t)std::max<int64_t>(cap, 1);
-    const size_t nsub = (size_t)p->nbins + (size_t)(cap / p->P) + 1;
-    if (cudaMalloc(&p->d_subp, nsub * sizeof(int4)) != cudaSuccess ||
+    if (cudaMalloc(&p->d_items, max_items(*p, cap) * sizeof(int4)) != cudaSuccess ||
         cudaMalloc(&p->d_local, c * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&p->d_binid, c * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&p->d_keyid, c * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&p->d_pidx, c * sizeof(int4)) != cudaSuccess ||
         cudaMalloc(&p->d_pfrac, c * sizeof(float4)) != cudaSuccess) {
         cudaGetLastError();
@@ -298,14 +315,19 @@ SortArgs sort_args(nufft_plan_s* p, const float* omega) {
         a.c_lo[d] = p->c_lo[d];
     }
     a.nbins = p->nbins;
+    a.cpb = p->cpb;
+    a.nkeys = p->nkeys;
     a.P = p->P;
-    a.count = p->d_count;
+    a.kcount = p->d_kcount;
+    a.bsum = p->d_bsum;
     a.local = p->d_local;
-    a.binid = p->d_binid;
+    a.keyid = p->d_keyid;
     a.offsets = p->d_offsets;
-    a.subp_off = p->d_subp_off;
-    a.subp = p->d_subp;
-    a.nsubp = p->d_nsubp;
+    a.item_off = p->d_item_off;
+    a.tile_parts = p->d_tile_parts;
+    a.tile_nbr = p->d_tile_nbr;
+    a.items = p->d_items;
+    a.nitems = p->d_nitems;
     a.pidx = p->d_pidx;
     a.pfrac = p->d_pfrac;
     return a;
@@ -324,11 +346,12 @@ int do_set_points(nufft_plan_s* p, int64_t m, const float* omega, cudaStream_t s
     p->last_stream = s;
     SortArgs a = sort_args(p, omega);
     int st;
-    if ((st = launch(p, PK_ZERO, s, [&] { return launch_zero(p->d_count, sizeof(int) * p->nbins, s); }))) return st;
-    if ((st = launch(p, PK_BIN_COUNT, s, [&] { return launch_bin_count(a, s); }))) return st;
-    if ((st = launch(p, PK_BIN_SCAN, s, [&] { return launch_bin_scan(a, s); }))) return st;
+    if ((st = launch(p, PK_ZERO, s, [&] { return launch_zero(p->d_kcount, sizeof(int) * p->nkeys, s); }))) return st;
+    if ((st = launch(p, PK_BIN_COUNT, s, [&] { return launch_key_count(a, s); }))) return st;
+    if ((st = launch(p, PK_BIN_SCAN, s, [&] { return launch_key_scan(a, s); }))) return st;
+    if ((st = launch(p, PK_TILE_SCAN, s, [&] { return launch_tile_scan(a, s); }))) return st;
     if ((st = launch(p, PK_BIN_SCATTER, s, [&] { return launch_bin_scatter(a, s); }))) return st;
-    if ((st = launch(p, PK_BIN_SUBPROB, s, [&] { return launch_bin_subprob(a, s); }))) return st;
+    if ((st = launch(p, PK_BIN_ITEMS, s, [&] { return launch_bin_items(a, s); }))) return st;
     return NUFFT_OK;
 }
 
@@ -416,9 +439,7 @@ int forward_grids(nufft_plan_s* p, int C, int nd, int has_plain, const float2* x
 int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, float2* xout, cudaStream_t s) {
     const int D = p->D;
     int st;
-    const size_t gbytes = (size_t)p->Ktot * C * sizeof(float2);
-    if ((st = launch(p, PK_ZERO, s, [&] { return launch_zero(p->d_G, gbytes, s); }))) return st;
-    // spread
+    // spread: output-driven tiles; only tiles split over several work items are cleared first
     SpreadArgs sa{};
     sa.pts = PointsView{p->d_pidx, p->d_pfrac, p->M};
     sa.D = D;
@@ -427,24 +448,33 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
         sa.K[d] = (int)p->K[d];
         sa.B[d] = p->B[d];
         sa.nb[d] = p->nb[d];
-        sa.T[d] = p->T[d];
     }
-    sa.subp = p->d_subp;
-    sa.nsubp = p->d_nsubp;
-    sa.max_subp = p->M > 0 ? p->nbins + (int)(p->M / p->P) + 1 : 0;
+    sa.nbins = p->nbins;
+    sa.offsets = p->d_offsets;
+    sa.tile_nbr = p->d_tile_nbr;
+    sa.items = p->d_items;
+    sa.nitems = p->d_nitems;
+    sa.tile_parts = p->d_tile_parts;
+    sa.max_items = (int)max_items(*p, p->M);
+    sa.P = p->P;
     sa.y = y;
     sa.M = p->M;
     sa.C = C;
     sa.CC = std::min(C, p->CCmax);
-    sa.G = std::min(32, pow2_ceil(sa.CC));
+    // row slots per warp: at least the kernel's minimum, at least 2 (<= 16 coils staged per pass)
+    sa.G = std::max(std::max(spread_min_slots(D, p->J), 2), 32 / std::min(32, pow2_ceil(sa.CC)));
     sa.lgG = ilog2(sa.G);
-    const int cpl = (sa.CC + sa.G - 1) / sa.G;
+    const int cpl = 1;
     sa.kb = p->kb;
     sa.grid = p->d_G;
-    size_t tcells = 1;
-    for (int d = 0; d < D; ++d) tcells *= p->T[d];
-    const size_t ssm = tcells * sa.CC * sizeof(float2) + (size_t)(256 / sa.G) * D * kJMax * sizeof(float);
-    if ((st = launch(p, PK_SPREAD, s, [&] { return launch_spread(sa, cpl, s, ssm); }))) return st;
+    const size_t ssm = (size_t)p->cpb * sa.CC * sizeof(float2);
+    if ((st = launch(p, PK_ZERO_HEAVY, s, [&] { return launch_zero_heavy_tiles(sa, s); }))) return st;
+    if (p->cell_spread) {
+        sa.CC = C <= 4 ? 4 : (C <= 8 ? 8 : 16);
+        if ((st = launch(p, PK_SPREAD, s, [&] { return launch_spread_cells(sa, s); }))) return st;
+    } else {
+        if ((st = launch(p, PK_SPREAD, s, [&] { return launch_spread(sa, cpl, s, ssm); }))) return st;
+    }
     // inverse FFT passes, dim 0 first; the last one crops, scales and applies maps
     const float2* in = p->d_G;
     ImageSide im = image_side(p, C, nullptr, smaps, xout, 0);
@@ -530,7 +560,7 @@ size_t nufft_workspace_bytes(const nufft_opts* o, int64_t m) {
     size_t G, T;
     workspace_elems(p, G, T);
     size_t b = (G + T) * sizeof(float2) + point_bytes(p, std::max<int64_t>(m, 1));
-    b += (size_t)(3 * p.nbins + 4) * sizeof(int);
+    b += (size_t)((3 + kNbrStride) * p.nbins + p.nkeys + p.nkeys / kScanPerBlock + 6) * sizeof(int);
     for (int d = 0; d < p.D; ++d) b += (size_t)p.N[d] * sizeof(float) + (size_t)p.K[d] * sizeof(float2);
     return b;
 }
@@ -565,12 +595,15 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
         build_fft_axis(L, p->axis[d]);
         p->axis[d].tw = p->d_tw[d];
     }
-    if (cudaMalloc(&p->d_count, sizeof(int) * p->nbins) != cudaSuccess ||
+    if (cudaMalloc(&p->d_kcount, sizeof(int) * p->nkeys) != cudaSuccess ||
+        cudaMalloc(&p->d_bsum, sizeof(int) * (p->nkeys / kScanPerBlock + 1)) != cudaSuccess ||
         cudaMalloc(&p->d_offsets, sizeof(int) * (p->nbins + 1)) != cudaSuccess ||
-        cudaMalloc(&p->d_subp_off, sizeof(int) * (p->nbins + 1)) != cudaSuccess ||
-        cudaMalloc(&p->d_nsubp, sizeof(int)) != cudaSuccess)
+        cudaMalloc(&p->d_item_off, sizeof(int) * (p->nbins + 1)) != cudaSuccess ||
+        cudaMalloc(&p->d_tile_parts, sizeof(int) * p->nbins) != cudaSuccess ||
+        cudaMalloc(&p->d_tile_nbr, sizeof(int) * kNbrStride * p->nbins) != cudaSuccess ||
+        cudaMalloc(&p->d_nitems, sizeof(int)) != cudaSuccess)
         return oom("bins");
-    cudaMemset(p->d_nsubp, 0, sizeof(int));
+    cudaMemset(p->d_nitems, 0, sizeof(int));
     workspace_elems(*p, p->G_elems, p->T_elems);
     if (cudaMalloc(&p->d_G, p->G_elems * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&p->d_T, p->T_elems * sizeof(float2)) != cudaSuccess)
@@ -802,10 +835,12 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
         o_deap[d] = cv.take<float>(p.N[d]);
         o_tw[d] = cv.take<float2>(p.K[d]);
     }
-    const size_t o_count = cv.take<int>(p.nbins), o_offsets = cv.take<int>(p.nbins + 1),
-                 o_subp_off = cv.take<int>(p.nbins + 1), o_nsubp = cv.take<int>(1),
-                 o_subp = cv.take<int4>((size_t)p.nbins + (size_t)(mc / p.P) + 1), o_local = cv.take<int>(mc),
-                 o_binid = cv.take<int>(mc), o_pidx = cv.take<int4>(mc), o_pfrac = cv.take<float4>(mc),
+    const size_t o_kcount = cv.take<int>(p.nkeys), o_bsum = cv.take<int>(p.nkeys / kScanPerBlock + 1),
+                 o_offsets = cv.take<int>(p.nbins + 1),
+                 o_item_off = cv.take<int>(p.nbins + 1), o_tile_parts = cv.take<int>(p.nbins),
+                 o_tile_nbr = cv.take<int>((size_t)kNbrStride * p.nbins),
+                 o_nitems = cv.take<int>(1), o_items = cv.take<int4>(max_items(p, mc)), o_local = cv.take<int>(mc),
+                 o_keyid = cv.take<int>(mc), o_pidx = cv.take<int4>(mc), o_pfrac = cv.take<float4>(mc),
                  o_G = cv.take<float2>(G), o_T = cv.take<float2>(T);
     if (cv.off > (size_t)NUFFT_NOALLOC_SCRATCH_BYTES)
         return fail(NUFFT_ERR_UNSUPPORTED, "problem needs " + std::to_string(cv.off) +
@@ -833,13 +868,16 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
         build_fft_axis(L, p.axis[d]);
         p.axis[d].tw = p.d_tw[d];
     }
-    p.d_count = (int*)(b + o_count);
+    p.d_kcount = (int*)(b + o_kcount);
+    p.d_bsum = (int*)(b + o_bsum);
     p.d_offsets = (int*)(b + o_offsets);
-    p.d_subp_off = (int*)(b + o_subp_off);
-    p.d_nsubp = (int*)(b + o_nsubp);
-    p.d_subp = (int4*)(b + o_subp);
+    p.d_item_off = (int*)(b + o_item_off);
+    p.d_tile_parts = (int*)(b + o_tile_parts);
+    p.d_tile_nbr = (int*)(b + o_tile_nbr);
+    p.d_nitems = (int*)(b + o_nitems);
+    p.d_items = (int4*)(b + o_items);
     p.d_local = (int*)(b + o_local);
-    p.d_binid = (int*)(b + o_binid);
+    p.d_keyid = (int*)(b + o_keyid);
     p.d_pidx = (int4*)(b + o_pidx);
     p.d_pfrac = (float4*)(b + o_pfrac);
     p.d_G = (float2*)(b + o_G);

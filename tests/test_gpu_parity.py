@@ -28,6 +28,15 @@ CASES = [
     ("2d_ragged", (30, 22), 37, 2, True, {}),
     ("3d_maps", (16, 20, 12), 2000, 2, True, {}),
     ("3d_multi_image", (12, 10, 14), 800, 3, False, {}),
+    ("2d_narrow_last_bin", (26, 30), 1500, 3, True, dict(bin_size=(16, 16))),      # K = 52, 60
+    ("3d_narrow_last_bin", (10, 14, 12), 900, 2, True, dict(bin_size=(8, 12, 8))),  # K = 20, 28, 24
+    ("2d_J4", (20, 24), 700, 2, True, dict(J=4)),
+    ("2d_J8", (20, 24), 700, 2, True, dict(J=8)),
+    ("2d_J7", (20, 24), 700, 2, True, dict(J=7)),
+    # one tile per axis: the general (atomic) spread kernel instead of the cell-owner one
+    ("2d_general_spread", (20, 24), 900, 3, True, dict(bin_size=(40, 48))),
+    ("3d_general_spread", (8, 10, 6), 500, 2, True, dict(bin_size=(16, 20, 12))),
+    ("2d_coils_6", (24, 24), 800, 6, True, {}),
 ]
 
 
@@ -36,10 +45,24 @@ def _plan(case, **opts):
     return Plan(case["shape"], to_dev(case["omega"]), max_coils=case["C"], **opts)
 
 
+def _clustered(shape, M, seed):
+    """Samples packed near the k-space centre: many work items per spread tile."""
+    g = np.random.default_rng(seed)
+    return np.clip(g.normal(0.0, 0.15, (len(shape), M)), -np.pi, np.pi).astype(np.float32)
+
+
+CASES += [
+    ("2d_clustered", (32, 32), 20000, 4, True, {}),
+    ("3d_clustered", (12, 12, 12), 8000, 2, True, {}),
+]
+
+
 @pytest.mark.parametrize("name,shape,M,C,maps,opts", CASES, ids=[c[0] for c in CASES])
 def test_all_products_match_same_kernel_oracle(name, shape, M, C, maps, opts):
     import torch
-    case = make_case(shape, M, C, maps, seed=sum(map(ord, name)))
+    seed = sum(map(ord, name))
+    om = _clustered(shape, M, seed) if "clustered" in name else None
+    case = make_case(shape, M, C, maps, seed=seed, omega=om)
     plan = _plan(case, **opts)
     X, S, V, Y, DOM = (to_dev(case[k]) for k in ("x", "smaps", "v", "y", "domega"))
     y = plan.forward(X, S)
@@ -48,7 +71,7 @@ def test_all_products_match_same_kernel_oracle(name, shape, M, C, maps, opts):
     dy_only = plan.jvp_omega(X, DOM, S)
     go, gx = plan.vjp_omega_x(X, V, S)
     torch.cuda.synchronize()
-    op = KBNufft(shape, case["omega"], **opts)
+    op = KBNufft(shape, case["omega"], **{k: v for k, v in opts.items() if k != "bin_size"})
     s = case["smaps"]
     y_ref = jb.sense_forward(op, case["x"], s)
     assert rel(host(y), y_ref) < TOL_SAME
