@@ -8,11 +8,15 @@
 // threads of a butterfly work on consecutive lines (conflict-free) and the
 // global loads and stores of a strided axis are coalesced along S.
 //
-// Stockham autosort, mixed radix (8, 4, 2, 3, 5): stage with radix R and
+// Stockham autosort, mixed radix (16, 8, 4, 2, 3, 5): stage with radix R and
 // running length Ns reads a[j + r L/R], twiddles by W^(r (j mod Ns) L/(Ns R)),
 // takes an R-point DFT and writes b[(j div Ns) Ns R + (j mod Ns) + r Ns].
 // Stages alternate between two shared buffers (ping-pong), one butterfly per
-// thread at a time, so register use is independent of the tile size.
+// thread at a time, so register use is independent of the tile size.  On the
+// grid side the first stage reads its R inputs straight from global memory and
+// the last stage writes its R outputs straight back (the last stage's output
+// positions are j + r L/R, the same pattern as the first stage's inputs), so a
+// pass costs (stages - 1) shared-memory round trips.
 //
 // Forward passes read N of the L input positions (zero padding: element e of
 // the image axis sits at position (e - N/2) mod L) and write all L; inverse
@@ -106,23 +110,97 @@ struct Dft<5, DIR> {
     }
 };
 
-template <int R, int DIR>
+template <int DIR>
+struct Dft<16, DIR> {
+    // 16 = 4 x 4: DFT4 over n1 for each n2, twiddle W16^(n2 k1), DFT4 over n2 for each k1.
+    __device__ __forceinline__ static void run(float2* a) {
+        const float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+        // W16^m = (cos 2pi m/16, DIR sin 2pi m/16) for m = 0..9
+        const float wc[10] = {1.f, c1, h, s1, 0.f, -s1, -h, -c1, -1.f, -c1};
+        const float ws[10] = {0.f, s1, h, c1, 1.f, c1, h, s1, 0.f, -s1};
+        float2 b[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            float2 t[4] = {a[n2], a[4 + n2], a[8 + n2], a[12 + n2]};
+            Dft<4, DIR>::run(t);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) {
+                const int m = n2 * k1;
+                if (m == 0) b[n2][k1] = t[k1];
+                else b[n2][k1] = cmul(t[k1], make_float2(wc[m], DIR * ws[m]));
+            }
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            float2 t[4] = {b[0][k1], b[1][k1], b[2][k1], b[3][k1]};
+            Dft<4, DIR>::run(t);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = t[k2];
+        }
+    }
+};
+
+// Global side of a fused first / last stage: tile line (lb, ls) is line
+// (b0 + lb, s0 + ls) of a [B][n][S] array; position p of the transform holds
+// element e(p) of the line (zero padding / crop: e = (p + n/2) mod L when p is
+// one of the n kept positions).
+struct LineIO {
+    const float2* in;
+    float2* out;
+    int64_t B, S, b0, s0;
+    int L, n_in, n_out, TS, lgTS;
+    bool pruned_in, cropped_out;
+
+    __device__ __forceinline__ float2 load(int line, int p) const {
+        const int lb = line >> lgTS, ls = line & (TS - 1);
+        const int64_t b = b0 + lb, s = s0 + ls;
+        int e = p;
+        if (pruned_in) {
+            const int h = n_in >> 1;
+            e = p < h ? p + h : (p >= L - h ? p - (L - h) : -1);
+        }
+        if (e < 0 || b >= B || s >= S) return make_float2(0.f, 0.f);
+        return in[(b * n_in + e) * S + s];
+    }
+    __device__ __forceinline__ void store(int line, int p, float2 v) const {
+        const int lb = line >> lgTS, ls = line & (TS - 1);
+        const int64_t b = b0 + lb, s = s0 + ls;
+        int e = p;
+        if (cropped_out) {
+            const int h = n_out >> 1;
+            e = p < h ? p + h : (p >= L - h ? p - (L - h) : -1);
+        }
+        if (e < 0 || b >= B || s >= S) return;
+        out[(b * n_out + e) * S + s] = v;
+    }
+};
+
+enum { ST_SMEM = 0, ST_GLOBAL = 1 };
+
+// One Stockham stage.  SRC / DST: shared tile or, for the first / last stage of
+// a pass, the global array itself (no shared round trip).
+template <int R, int DIR, int SRC, int DST>
 __device__ __forceinline__ void fft_stage(const float2* __restrict__ src, float2* __restrict__ dst,
-                                          const float2* __restrict__ tw, int L, int TLP, int lgTL, const FftStage st) {
+                                          const float2* __restrict__ tw, int L, int TLP, int lgTL, const FftStage st,
+                                          const LineIO& io) {
     const int LR = L / R;
     const int TL = 1 << lgTL;
     const int total = LR << lgTL;
     const int sstride = LR * TLP, dstride = st.Ns * TLP;
-#pragma unroll 2
     for (int u = threadIdx.x; u < total; u += blockDim.x) {
         const int line = u & (TL - 1);
         const int j = u >> lgTL;
         const int jq = (int)div_magic((uint32_t)j, (uint32_t)st.Ns, st.magic);
         const int kk = j - jq * st.Ns;
         float2 v[R];
-        const float2* sp = src + j * TLP + line;
+        if (SRC == ST_SMEM) {
+            const float2* sp = src + j * TLP + line;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = sp[r * sstride];
+            for (int r = 0; r < R; ++r) v[r] = sp[r * sstride];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = io.load(line, j + r * LR);
+        }
         if (st.Ns > 1) {
             const int tstep = kk * st.tw_step;
 #pragma unroll
@@ -133,27 +211,46 @@ __device__ __forceinline__ void fft_stage(const float2* __restrict__ src, float2
             }
         }
         Dft<R, DIR>::run(v);
-        float2* dp = dst + (jq * st.Ns * R + kk) * TLP + line;
+        const int d0 = jq * st.Ns * R + kk;
+        if (DST == ST_SMEM) {
+            float2* dp = dst + d0 * TLP + line;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dp[r * dstride] = v[r];
+            for (int r = 0; r < R; ++r) dp[r * dstride] = v[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) io.store(line, d0 + r * st.Ns, v[r]);
+        }
     }
     __syncthreads();
 }
 
-// Runs all stages; returns the buffer that holds the result.
+template <int R, int DIR>
+__device__ __forceinline__ void fft_stage_any(bool gin, bool gout, const float2* src, float2* dst, const float2* tw,
+                                              int L, int TLP, int lgTL, const FftStage st, const LineIO& io) {
+    if (gin && gout) fft_stage<R, DIR, ST_GLOBAL, ST_GLOBAL>(src, dst, tw, L, TLP, lgTL, st, io);
+    else if (gin) fft_stage<R, DIR, ST_GLOBAL, ST_SMEM>(src, dst, tw, L, TLP, lgTL, st, io);
+    else if (gout) fft_stage<R, DIR, ST_SMEM, ST_GLOBAL>(src, dst, tw, L, TLP, lgTL, st, io);
+    else fft_stage<R, DIR, ST_SMEM, ST_SMEM>(src, dst, tw, L, TLP, lgTL, st, io);
+}
+
+// Runs all stages.  gin: the first stage reads the global input; gout: the last
+// stage writes the global output.  Returns the shared buffer holding the result
+// when !gout.
 template <int DIR>
 __device__ float2* fft_all_stages(float2* buf0, float2* buf1, const float2* tw, const FftStage* sst, int nstages,
-                                  int L, int TLP, int lgTL) {
+                                  int L, int TLP, int lgTL, bool gin, bool gout, const LineIO& io) {
     float2* src = buf0;
     float2* dst = buf1;
     for (int s = 0; s < nstages; ++s) {
         const FftStage st = sst[s];
+        const bool fi = gin && s == 0, fo = gout && s == nstages - 1;
         switch (st.R) {
-            case 8: fft_stage<8, DIR>(src, dst, tw, L, TLP, lgTL, st); break;
-            case 4: fft_stage<4, DIR>(src, dst, tw, L, TLP, lgTL, st); break;
-            case 2: fft_stage<2, DIR>(src, dst, tw, L, TLP, lgTL, st); break;
-            case 3: fft_stage<3, DIR>(src, dst, tw, L, TLP, lgTL, st); break;
-            default: fft_stage<5, DIR>(src, dst, tw, L, TLP, lgTL, st); break;
+            case 16: fft_stage_any<16, DIR>(fi, fo, src, dst, tw, L, TLP, lgTL, st, io); break;
+            case 8: fft_stage_any<8, DIR>(fi, fo, src, dst, tw, L, TLP, lgTL, st, io); break;
+            case 4: fft_stage_any<4, DIR>(fi, fo, src, dst, tw, L, TLP, lgTL, st, io); break;
+            case 2: fft_stage_any<2, DIR>(fi, fo, src, dst, tw, L, TLP, lgTL, st, io); break;
+            case 3: fft_stage_any<3, DIR>(fi, fo, src, dst, tw, L, TLP, lgTL, st, io); break;
+            default: fft_stage_any<5, DIR>(fi, fo, src, dst, tw, L, TLP, lgTL, st, io); break;
         }
         float2* t = src;
         src = dst;
@@ -181,7 +278,7 @@ __device__ __forceinline__ void image_row(int D, int N0, int N1, const float* de
 }
 
 template <PassKind KIND>
-__global__ void __launch_bounds__(512) k_line_fft(LinePass a) {
+__global__ void __launch_bounds__(256) k_line_fft(LinePass a) {
     constexpr int DIR = (KIND == PASS_FWD_FIRST || KIND == PASS_FWD_MID) ? -1 : 1;
     extern __shared__ float2 smem[];
     const int L = a.ax.L;
@@ -223,61 +320,51 @@ __global__ void __launch_bounds__(512) k_line_fft(LinePass a) {
 
     for (int chunk = 0; chunk < nchunks; ++chunk) {
         const int64_t s0 = (a.coil_sum ? (int64_t)chunk : (int64_t)blockIdx.y) * TS;
-        // ---------------- prologue: fill the tile, zero padding included
-        const int nfill = L * TL;
+        LineIO io;
+        io.in = a.in;
+        io.out = a.out;
+        io.B = a.B;
+        io.S = a.S;
+        io.b0 = b0;
+        io.s0 = s0;
+        io.L = L;
+        io.n_in = a.n_in;
+        io.n_out = a.n_out;
+        io.TS = TS;
+        io.lgTS = a.lgTS;
+        io.pruned_in = DIR < 0;
+        io.cropped_out = DIR > 0;
+        // ---------------- prologue: the first pass builds the tile from the image
+        const int nfill = KIND == PASS_FWD_FIRST ? L * TL : 0;
         for (int f = tid; f < nfill; f += nt) {
-            int p, lb, ls;
-            if (KIND == PASS_FWD_FIRST) {   // image side: positions fastest
-                const int line = (int)div_magic((uint32_t)f, (uint32_t)L, a.magic_L);
-                p = f - line * L;
-                lb = line >> a.lgTS;
-                ls = line & (TS - 1);
-            } else {                         // grid side: lines fastest
-                ls = f & (TS - 1);
-                const int rest = f >> a.lgTS;
-                lb = (int)div_magic((uint32_t)rest, (uint32_t)L, a.magic_L);
-                p = rest - lb * L;
-            }
-            int e;
-            if (DIR < 0) e = p < half_in ? p + half_in : (p >= L - half_in ? p - (L - half_in) : -1);
-            else e = p;
+            // positions fastest: image rows are contiguous
+            const int line = (int)div_magic((uint32_t)f, (uint32_t)L, a.magic_L);
+            const int p = f - line * L;
+            const int lb = line >> a.lgTS, ls = line & (TS - 1);
+            const int e = p < half_in ? p + half_in : (p >= L - half_in ? p - (L - half_in) : -1);
             float2 val = make_float2(0.f, 0.f);
             const int64_t b = b0 + lb, s = s0 + ls;
             if (e >= 0 && b < a.B && s < a.S) {
-                if (KIND == PASS_FWD_FIRST) {
-                    const int dblk = (int)(s / a.im.C), c = (int)(s - (int64_t)dblk * a.im.C);
-                    const int kind = a.im.has_plain ? dblk - 1 : dblk;   // -1: plain image
-                    const int64_t pix = b * nlast + e;
-                    float2 xv = a.im.smaps ? cmul(a.im.x[pix], a.im.smaps[(int64_t)c * a.im.nimg + pix])
-                                           : a.im.x[(int64_t)c * a.im.nimg + pix];
-                    float sc = row_scale[lb] * deap_last[e];
-                    if (kind == Dm1) sc *= (float)(e - nlast / 2);
-                    else if (kind >= 0) sc *= row_r[2 * lb + kind];
-                    val = cscale(xv, sc);
-                } else {
-                    val = a.in[(b * a.n_in + e) * a.S + s];
-                }
+                const int dblk = (int)(s / a.im.C), c = (int)(s - (int64_t)dblk * a.im.C);
+                const int kind = a.im.has_plain ? dblk - 1 : dblk;   // -1: plain image
+                const int64_t pix = b * nlast + e;
+                float2 xv = a.im.smaps ? cmul(a.im.x[pix], a.im.smaps[(int64_t)c * a.im.nimg + pix])
+                                       : a.im.x[(int64_t)c * a.im.nimg + pix];
+                float sc = row_scale[lb] * deap_last[e];
+                if (kind == Dm1) sc *= (float)(e - nlast / 2);
+                else if (kind >= 0) sc *= row_r[2 * lb + kind];
+                val = cscale(xv, sc);
             }
             buf[p * TLP + lb * TS + ls] = val;
         }
         __syncthreads();
 
-        const float2* res = fft_all_stages<DIR>(buf, buf1, tw, sst, nstages, L, TLP, a.lgTL);
+        const bool gin = KIND != PASS_FWD_FIRST, gout = KIND != PASS_INV_LAST;
+        const float2* res = fft_all_stages<DIR>(buf, buf1, tw, sst, nstages, L, TLP, a.lgTL, gin, gout, io);
 
         // ---------------- epilogue
         const int half_out = a.n_out / 2;
-        if (KIND == PASS_FWD_FIRST || KIND == PASS_FWD_MID || KIND == PASS_INV_MID) {
-            const int nst = a.n_out * TL;
-            for (int f = tid; f < nst; f += nt) {
-                const int ls = f & (TS - 1);
-                const int rest = f >> a.lgTS;
-                const int lb = (int)div_magic((uint32_t)rest, (uint32_t)a.n_out, a.magic_n);
-                const int e = rest - lb * a.n_out;
-                const int p = (DIR < 0) ? e : (e < half_out ? e + L - half_out : e - half_out);
-                const int64_t b = b0 + lb, s = s0 + ls;
-                if (b < a.B && s < a.S) a.out[(b * a.n_out + e) * a.S + s] = res[p * TLP + lb * TS + ls];
-            }
-        } else {   // PASS_INV_LAST: crop, scale, coil maps
+        if (KIND == PASS_INV_LAST) {   // crop, scale, coil maps
             if (a.coil_sum) {
                 const int nst = a.n_out * TB;
                 for (int f = tid; f < nst; f += nt) {

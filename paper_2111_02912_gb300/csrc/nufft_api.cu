@@ -147,6 +147,7 @@ int launch(nufft_plan_s* p, int kind, cudaStream_t s, F&& f) {
 void build_fft_axis(int L, FftAxis& ax) {
     std::vector<int> rad;
     int q = L;
+    while (q % 16 == 0) { rad.push_back(16); q /= 16; }
     while (q % 8 == 0) { rad.push_back(8); q /= 8; }
     while (q % 4 == 0) { rad.push_back(4); q /= 4; }
     while (q % 2 == 0) { rad.push_back(2); q /= 2; }
@@ -368,9 +369,8 @@ Tile pick_tile(int L, int64_t B, int64_t S, bool coil_sum, int n_out) {
     t.TS = std::min<int>(TL, pow2_ceil(S));
     t.TB = std::min<int>(TL / t.TS, pow2_ceil(B));
     t.TL = t.TB * t.TS;
-    int work = (L / 2) * t.TL;   // butterflies of a radix-2 stage
-    t.threads = std::min(512, std::max(64, ((work + 31) / 32) * 32));
-    if (t.threads > 256 && work < 512) t.threads = 256;
+    int work = (L / 4) * t.TL;   // butterflies of a radix-4 stage
+    t.threads = std::min(256, std::max(64, ((work + 31) / 32) * 32));
     t.smem = (size_t)(L + 2 * (size_t)L * (t.TL + 1)) * sizeof(float2) + (size_t)t.TB * 3 * sizeof(float);
     if (coil_sum) t.smem += (size_t)t.TB * n_out * sizeof(float2);
     return t;
