@@ -93,6 +93,7 @@ struct ImageSide {
     int N[kMaxDim];
     const float* deap[kMaxDim];   // per-dim scaling factors s_d[n]
     int64_t nimg;          // prod N
+    int64_t xout_stride;   // coil-sum pass: partial image of channel chunk y at xout + y * xout_stride
 };
 
 struct LinePass {
@@ -111,6 +112,8 @@ struct LinePass {
 enum PassKind { PASS_FWD_FIRST, PASS_FWD_MID, PASS_INV_MID, PASS_INV_LAST };
 cudaError_t launch_line_pass(PassKind kind, const LinePass& a, dim3 grid, int threads, size_t smem,
                              cudaStream_t s);
+// x[i] = sum_k part[k * n + i] for k < nparts, in order (the coil-sum chunks of PASS_INV_LAST).
+cudaError_t launch_sum_chunks(const float2* part, int nparts, int64_t n, float2* x, cudaStream_t s);
 
 // ---------------------------------------------------------- interpolation
 enum GatherMode { GM_FWD = 0, GM_JVP = 1, GM_VJP = 2 };

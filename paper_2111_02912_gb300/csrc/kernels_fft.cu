@@ -24,6 +24,8 @@
 // builds its input from the image (scaling s_n of the Appendix, coil map s_c
 // of Sec. II-G and coordinate weight r^[d] of Eq. (e,Ax)); the last inverse
 // pass applies the scaling, conj(s_c) and the coil sum.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace nj {
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(256) k_line_fft(LinePass a) {
     const int nchunks = a.nchunks;
 
     for (int chunk = 0; chunk < nchunks; ++chunk) {
-        const int64_t s0 = (a.coil_sum ? (int64_t)chunk : (int64_t)blockIdx.y) * TS;
+        const int64_t s0 = ((int64_t)blockIdx.y * nchunks + chunk) * TS;
         LineIO io;
         io.in = a.in;
         io.out = a.out;
@@ -399,12 +401,28 @@ __global__ void __launch_bounds__(256) k_line_fft(LinePass a) {
         __syncthreads();
     }
     if (KIND == PASS_INV_LAST && a.coil_sum) {
+        float2* xo = a.im.xout + (int64_t)blockIdx.y * a.im.xout_stride;
         for (int f = tid; f < TB * a.n_out; f += nt) {
             const int lb = f / a.n_out, e = f - lb * a.n_out;
             const int64_t b = b0 + lb;
-            if (b < a.B) a.im.xout[b * nlast + e] = cscale(acc[f], row_scale[lb] * deap_last[e]);
+            if (b < a.B) xo[b * nlast + e] = cscale(acc[f], row_scale[lb] * deap_last[e]);
         }
     }
+}
+
+__global__ void k_sum_chunks(const float2* __restrict__ part, int nparts, int64_t n, float2* __restrict__ x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float2 acc = part[i];
+        for (int k = 1; k < nparts; ++k) acc = cadd(acc, part[(int64_t)k * n + i]);
+        x[i] = acc;
+    }
+}
+
+cudaError_t launch_sum_chunks(const float2* part, int nparts, int64_t n, float2* x, cudaStream_t s) {
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    k_sum_chunks<<<blocks, 256, 0, s>>>(part, nparts, n, x);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_line_pass(PassKind kind, const LinePass& a, dim3 grid, int threads, size_t smem,

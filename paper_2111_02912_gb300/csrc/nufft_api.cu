@@ -36,11 +36,11 @@ int fail(int status, const std::string& msg) {
 
 enum ProfKind {
     PK_ZERO, PK_BIN_COUNT, PK_BIN_SCAN, PK_TILE_SCAN, PK_BIN_SCATTER, PK_BIN_ITEMS, PK_FFT_FWD_FIRST, PK_FFT_FWD_MID,
-    PK_FFT_INV_MID, PK_FFT_INV_LAST, PK_GATHER_FWD, PK_GATHER_JVP, PK_GATHER_VJP, PK_ZERO_HEAVY, PK_SPREAD, PK_COUNT
+    PK_FFT_INV_MID, PK_FFT_INV_LAST, PK_GATHER_FWD, PK_GATHER_JVP, PK_GATHER_VJP, PK_ZERO_HEAVY, PK_SPREAD, PK_SUM_CHUNKS, PK_COUNT
 };
 const char* kProfNames[PK_COUNT] = {"zero", "bin_count", "bin_scan", "tile_scan", "bin_scatter", "bin_items", "fft_fwd_first",
                                     "fft_fwd_mid", "fft_inv_mid", "fft_inv_last", "gather_fwd", "gather_jvp",
-                                    "gather_vjp", "zero_heavy", "spread"};
+                                    "gather_vjp", "zero_heavy", "spread", "sum_chunks"};
 
 int64_t grid_size(int64_t n, double sigma) {
     int64_t k = (int64_t)std::ceil(sigma * (double)n - 1e-9);
@@ -271,7 +271,9 @@ void workspace_elems(const nufft_plan_s& p, size_t& G, size_t& T) {
         if ((d % 2) == 0) T = std::max<size_t>(T, (size_t)(n * p.maxC));
         else G = std::max<size_t>(G, (size_t)(n * p.maxC));
     }
-    if (T == 0) T = 1;
+    // the coil-summing last inverse pass keeps up to C partial images in the buffer it does not read
+    T = std::max<size_t>(T, (size_t)(p.maxC * p.Nimg));
+    G = std::max<size_t>(G, (size_t)(p.maxC * p.Nimg));
 }
 
 // Upper bound of the spread work items: one per tile plus one per P candidates;
@@ -362,7 +364,7 @@ struct Tile {
     size_t smem;
 };
 Tile pick_tile(int L, int64_t B, int64_t S, bool coil_sum, int n_out) {
-    const size_t budget = 100 * 1024;
+    const size_t budget = 58 * 1024;   // three to four blocks per SM
     int TL = 32;
     while (TL > 1 && (size_t)(2 * (size_t)L * (TL + 1) + L) * sizeof(float2) > budget) TL /= 2;
     Tile t;
@@ -499,17 +501,28 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
         a.lgTL = ilog2(t.TL);
         a.TLP = t.TL + 1;
         a.coil_sum = coil_sum ? 1 : 0;
-        a.nchunks = coil_sum ? (int)((S + t.TS - 1) / t.TS) : 1;
+        a.nchunks = 1;   // one channel chunk per block; chunks are blockIdx.y
+        const int chunks = (int)((S + t.TS - 1) / t.TS);
         a.in = in;
         a.out = out;
         a.im = im;
+        float2* part = nullptr;
+        if (coil_sum && chunks > 1) {   // partial coil sums per chunk, added in order afterwards
+            part = (in == p->d_G) ? p->d_T : p->d_G;
+            a.im.xout = part;
+            a.im.xout_stride = p->Nimg;
+        }
         a.magic_L = magic_of((uint32_t)L);
         a.magic_n = magic_of((uint32_t)a.n_out);
-        dim3 grid((unsigned)((B + t.TB - 1) / t.TB), coil_sum ? 1u : (unsigned)((S + t.TS - 1) / t.TS));
+        dim3 grid((unsigned)((B + t.TB - 1) / t.TB), (unsigned)chunks);
         const PassKind kind = last ? PASS_INV_LAST : PASS_INV_MID;
         st = launch(p, last ? PK_FFT_INV_LAST : PK_FFT_INV_MID, s,
                     [&] { return launch_line_pass(kind, a, grid, t.threads, t.smem, s); });
         if (st) return st;
+        if (part) {
+            st = launch(p, PK_SUM_CHUNKS, s, [&] { return launch_sum_chunks(part, chunks, p->Nimg, xout, s); });
+            if (st) return st;
+        }
         in = out;
     }
     return NUFFT_OK;

@@ -37,6 +37,8 @@ CASES = [
     ("2d_general_spread", (20, 24), 900, 3, True, dict(bin_size=(40, 48))),
     ("3d_general_spread", (8, 10, 6), 500, 2, True, dict(bin_size=(16, 20, 12))),
     ("2d_coils_6", (24, 24), 800, 6, True, {}),
+    ("2d_tiny_grid_J8", (8, 10), 300, 3, True, dict(J=8)),   # K = 16, 20: tiles wrap more than once
+    ("2d_coils_40_jvp", (16, 20), 500, 40, True, {}),        # several coil chunks in every kernel
 ]
 
 
