@@ -135,6 +135,7 @@ struct GatherArgs {
 cudaError_t launch_gather_d1(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);
 cudaError_t launch_gather_d2(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);
 cudaError_t launch_gather_d3(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);
+// cpl: 0 = coil pairs (C even, C <= 64, G >= C / 2), 1 = one coil per lane (C <= G), else 4.
 inline cudaError_t launch_gather(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s) {
     return a.D == 1 ? launch_gather_d1(mode, a, cpl, s)
                     : (a.D == 2 ? launch_gather_d2(mode, a, cpl, s) : launch_gather_d3(mode, a, cpl, s));

@@ -28,7 +28,9 @@ __device__ __forceinline__ void group_weights(float* w, const float* coef, float
     }
 }
 
-template <int D, int J, int ND, int CPL, int MODE>
+// PAIR: lane l owns the coil pairs (2 (l + k G), 2 (l + k G) + 1), read as one 16-byte load
+// (C even); otherwise lane l owns coils l + k G.
+template <int D, int J, int ND, int CPL, int MODE, bool PAIR>
 __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
     __shared__ float coef[kKbTerms];
     extern __shared__ float wsm[];   // [groups][D * J]
@@ -53,14 +55,17 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
 
     const int C = a.C;
     const int chs = ND * C;   // channel stride of one grid cell
+    constexpr int W = PAIR ? 2 : 1;   // coils per lane slot
     bool ok[CPL];
 #pragma unroll
-    for (int k = 0; k < CPL; ++k) ok[k] = lane_g + k * G < C;
-    float2 acc[ND][CPL];
+    for (int k = 0; k < CPL; ++k) ok[k] = W * (lane_g + k * G) < C;
+    float2 acc[ND][CPL][W];
 #pragma unroll
     for (int q = 0; q < ND; ++q)
 #pragma unroll
-        for (int k = 0; k < CPL; ++k) acc[q][k] = make_float2(0.f, 0.f);
+        for (int k = 0; k < CPL; ++k)
+#pragma unroll
+            for (int i = 0; i < W; ++i) acc[q][k][i] = make_float2(0.f, 0.f);
 
     // innermost axis: column offsets and weights in registers
     const int Kl = a.K[D - 1];
@@ -74,7 +79,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
         coff[j] = k * chs;
         wl[j] = w[(D - 1) * J + j];
     }
-    const float2* g0 = a.grid + lane_g;
+    const float2* g0 = a.grid + W * lane_g;
 
     auto row = [&](const float2* rp, float wr) {
 #pragma unroll
@@ -86,9 +91,17 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
 #pragma unroll
                 for (int k = 0; k < CPL; ++k)
                     if (ok[k]) {
-                        const float2 g = __ldg(gp + q * C + k * G);
-                        acc[q][k].x = fmaf(wt, g.x, acc[q][k].x);
-                        acc[q][k].y = fmaf(wt, g.y, acc[q][k].y);
+                        if (PAIR) {
+                            const float4 g = __ldg((const float4*)(gp + q * C + 2 * k * G));
+                            acc[q][k][0].x = fmaf(wt, g.x, acc[q][k][0].x);
+                            acc[q][k][0].y = fmaf(wt, g.y, acc[q][k][0].y);
+                            acc[q][k][W - 1].x = fmaf(wt, g.z, acc[q][k][W - 1].x);
+                            acc[q][k][W - 1].y = fmaf(wt, g.w, acc[q][k][W - 1].y);
+                        } else {
+                            const float2 g = __ldg(gp + q * C + k * G);
+                            acc[q][k][0].x = fmaf(wt, g.x, acc[q][k][0].x);
+                            acc[q][k][0].y = fmaf(wt, g.y, acc[q][k][0].y);
+                        }
                     }
         }
     };
@@ -127,7 +140,9 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
     if (MODE == GM_FWD) {
 #pragma unroll
         for (int k = 0; k < CPL; ++k)
-            if (ok[k]) a.y[(int64_t)(lane_g + k * G) * M + orig] = acc[0][k];
+#pragma unroll
+            for (int i = 0; i < W; ++i)
+                if (ok[k]) a.y[(int64_t)(W * (lane_g + k * G) + i) * M + orig] = acc[0][k][i];
     } else if (MODE == GM_JVP) {
         float dom[D];
 #pragma unroll
@@ -135,16 +150,19 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
             if (!ok[k]) continue;
-            const int64_t c = lane_g + k * G;
-            float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const float2 g = acc[(ND > D ? 1 : 0) + d][k];
-                s.x = fmaf(dom[d], g.y, s.x);    // -i * g = (g.y, -g.x)
-                s.y = fmaf(-dom[d], g.x, s.y);
+            for (int i = 0; i < W; ++i) {
+                const int64_t c = W * (lane_g + k * G) + i;
+                float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const float2 g = acc[(ND > D ? 1 : 0) + d][k][i];
+                    s.x = fmaf(dom[d], g.y, s.x);    // -i * g = (g.y, -g.x)
+                    s.y = fmaf(-dom[d], g.x, s.y);
+                }
+                a.dy[c * M + orig] = s;
+                if (ND > D) a.y[c * M + orig] = acc[0][k][i];
             }
-            a.dy[c * M + orig] = s;
-            if (ND > D) a.y[c * M + orig] = acc[0][k];
         }
     } else {   // GM_VJP
         float gsum[D];
@@ -153,11 +171,14 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
             if (!ok[k]) continue;
-            const float2 v = __ldg(a.v + (int64_t)(lane_g + k * G) * M + orig);
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const float2 g = acc[d][k];
-                gsum[d] += v.x * g.y - v.y * g.x;   // Im{conj(v) g}
+            for (int i = 0; i < W; ++i) {
+                const float2 v = __ldg(a.v + (int64_t)(W * (lane_g + k * G) + i) * M + orig);
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const float2 g = acc[d][k][i];
+                    gsum[d] += v.x * g.y - v.y * g.x;   // Im{conj(v) g}
+                }
             }
         }
         const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) & ~(G - 1)));
@@ -178,8 +199,9 @@ static cudaError_t gather_cpl(const GatherArgs& a, int cpl, cudaStream_t s) {
     const unsigned blocks = (unsigned)((a.pts.m + gpb - 1) / gpb);
     const size_t smem = (size_t)gpb * D * J * sizeof(float);
     if (blocks == 0) return cudaSuccess;
-    if (cpl == 1) k_gather<D, J, ND, 1, MODE><<<blocks, threads, smem, s>>>(a);
-    else k_gather<D, J, ND, 4, MODE><<<blocks, threads, smem, s>>>(a);   // C up to 4 G = 128
+    if (cpl == 0) k_gather<D, J, ND, 1, MODE, true><<<blocks, threads, smem, s>>>(a);   // coil pairs
+    else if (cpl == 1) k_gather<D, J, ND, 1, MODE, false><<<blocks, threads, smem, s>>>(a);
+    else k_gather<D, J, ND, 4, MODE, false><<<blocks, threads, smem, s>>>(a);   // C up to 4 G = 128
     return cudaGetLastError();
 }
 

@@ -538,11 +538,17 @@ GatherArgs gather_args(nufft_plan_s* p, int C, int nd, int has_plain) {
     g.C = C;
     g.nd = nd;
     g.has_plain = has_plain;
-    g.G = std::min(32, pow2_ceil(C));
+    // even C up to 64: a lane owns two adjacent coils (16-byte loads), else one
+    g.G = (C % 2 == 0 && C <= 64) ? pow2_ceil(C / 2) : std::min(32, pow2_ceil(C));
     g.lgG = ilog2(g.G);
     g.kb = p->kb;
     g.M = p->M;
     return g;
+}
+
+int gather_cpl(const GatherArgs& g) {
+    if (g.C % 2 == 0 && g.C <= 64) return 0;
+    return (g.C + g.G - 1) / g.G;
 }
 
 int check_call(nufft_plan_s* p, int C) {
@@ -643,7 +649,7 @@ int nufft_forward(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cflo
     if ((st = forward_grids(p, C, 1, 1, (const float2*)x, (const float2*)smaps, s))) return st;
     GatherArgs g = gather_args(p, C, 1, 1);
     g.y = (float2*)y;
-    const int cpl = (C + g.G - 1) / g.G;
+    const int cpl = gather_cpl(g);
     return launch(p, PK_GATHER_FWD, s, [&] { return launch_gather(GM_FWD, g, cpl, s); });
 }
 
@@ -672,7 +678,7 @@ int nufft_jvp_omega(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cf
     g.y = (float2*)y_or_null;
     g.dy = (float2*)dy;
     g.domega = domega;
-    const int cpl = (C + g.G - 1) / g.G;
+    const int cpl = gather_cpl(g);
     return launch(p, PK_GATHER_JVP, s, [&] { return launch_gather(GM_JVP, g, cpl, s); });
 }
 
@@ -688,7 +694,7 @@ int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_
         GatherArgs g = gather_args(p, C, p->D, 0);
         g.v = (const float2*)v;
         g.grad = grad_omega;
-        const int cpl = (C + g.G - 1) / g.G;
+        const int cpl = gather_cpl(g);
         if ((st = launch(p, PK_GATHER_VJP, s, [&] { return launch_gather(GM_VJP, g, cpl, s); }))) return st;
     }
     if (grad_x) return adjoint_impl(p, C, (const float2*)v, (const float2*)smaps, (float2*)grad_x, s);
@@ -904,6 +910,6 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
     if ((st = forward_grids(&p, C, 1, 1, (const float2*)x, (const float2*)smaps, s))) return st;
     GatherArgs g = gather_args(&p, C, 1, 1);
     g.y = (float2*)y;
-    const int cpl = (C + g.G - 1) / g.G;
+    const int cpl = gather_cpl(g);
     return launch(&p, PK_GATHER_FWD, s, [&] { return launch_gather(GM_FWD, g, cpl, s); });
 }
