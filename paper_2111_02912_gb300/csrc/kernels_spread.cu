@@ -261,12 +261,14 @@ __global__ void __launch_bounds__(256, 2) k_spread(SpreadArgs a) {
 // (every tile edge Bt_d <= K_d - J + 1) and tiles are at least J - 1 wide.
 // The block stages the work item's candidates (one per thread), keeps those
 // whose window reaches the tile, and counting-sorts them in shared memory by
-// window start, in coordinates e_d = start_d - org_d + J - 1 in [0, Bt_d + J - 1).
-// Thread t then owns tile cell t for CPT coils: the points covering cell l are
-// those with e_d in [l_d, l_d + J - 1] for every axis, with tap j_d = l_d + J - 1 - e_d,
-// so it sums w * y over the J^D start cells around it in registers.  No
-// atomics on the tile; within a start cell the points are summed in the order
-// they were placed (rounding-level differences between runs).
+// window-start row, in coordinates e_d = start_d - org_d + J - 1 in
+// [0, Bt_d + J - 1) (the row is e_0 in 2-D, (e_0, e_1) in 3-D).  Thread t then
+// owns tile cell t for CPT coils: the points covering cell l are those with
+// e_d in [l_d, l_d + J - 1] for every axis, with tap j_d = l_d + J - 1 - e_d,
+// so it visits the J (2-D) or J^2 (3-D) rows around it, keeps the points whose
+// last coordinate fits, and sums w * y in registers.  No atomics on the tile;
+// within a row the points are summed in the order they were placed
+// (rounding-level differences between runs).
 template <int D, int J, int CPT>
 __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
     extern __shared__ float4 smem4[];
@@ -290,15 +292,16 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
             E[d] = Bt[d] + J - 1;
         }
     }
-    const int NE = E[0] * E[1] * E[2];     // start-cell bins of this tile
+    // row bins: all start coordinates but the last (E0 in 2-D, E0 * E1 in 3-D)
+    const int NR = D == 2 ? E[0] : E[0] * E[1];
     const int P = a.P;
     const int c0 = blockIdx.y * CPT;
     const int ncc = min(CPT, a.C - c0);
-    // shared layout: weights [P][D*J], y [P][CPT+1], bin of each hit [P], sorted hits [P], counts [NE+1]
+    // shared layout: weights [P][D*J], y [P][CPT+1], last start coordinate [P], sorted hits [P], row cursors [NR+1]
     float* s_w = (float*)smem4;
     float2* s_y = (float2*)(s_w + P * D * J + ((P * D * J) & 1));
-    int* s_e = (int*)(s_y + (size_t)P * (CPT + 1));
-    int* s_list = s_e + P;
+    int* s_el = (int*)(s_y + (size_t)P * (CPT + 1));
+    int* s_list = s_el + P;
     int* s_cnt = s_list + P;
 
     if (tid < kKbTerms) coef[tid] = a.kb.a[tid];
@@ -308,33 +311,33 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
         if (tid < 27) s_start[tid] = tn[1 + 2 * tid];      // entries past the count are never used
         if (tid < 28) s_pref[tid] = tn[2 + 2 * tid];
     }
-    for (int i = tid; i <= NE; i += nt) s_cnt[i] = 0;
+    for (int i = tid; i <= NR; i += nt) s_cnt[i] = 0;
     __syncthreads();
 
     // stage: thread t takes candidate lo + t
     const int nn = s_nn;
     const int lo = part * P, hi = min(s_pref[nn], lo + P);
     const int cand = lo + tid;
-    int my_e = -1;
-    int my_slot = -1;
+    int my_row = -1, my_slot = -1;
     if (tid < P && cand < hi) {
         int q = 0;
         while (q + 1 < nn && s_pref[q + 1] <= cand) ++q;
         const int64_t p = s_start[q] + (cand - s_pref[q]);
         const int4 ix = a.pts.idx[p];
         bool hit = true;
-        int e = 0;
+        int e[kMaxDim] = {0, 0, 0};
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             int sd = (d == 0 ? ix.x : (d == 1 ? ix.y : ix.z)) - org[d];
             if (sd < 0) sd += Kd[d];
             if (sd > Kd[d] - J) sd -= Kd[d];           // starts up to J-1 cells before the tile
             hit = hit && sd >= -(J - 1) && sd < Bt[d];
-            e = e * E[d] + (sd + J - 1);
+            e[d] = sd + J - 1;
         }
         if (hit) {
             my_slot = atomicAdd(&s_nh, 1);
-            my_e = e;
+            my_row = D == 2 ? e[0] : e[0] * E[1] + e[1];
+            s_el[my_slot] = e[D - 1];
             const float4 fr = a.pts.frac[p];
             float* w = s_w + my_slot * (D * J);
 #pragma unroll
@@ -347,16 +350,15 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
 #pragma unroll
             for (int c = 0; c < CPT; ++c)
                 yv[c] = c < ncc ? __ldg(a.y + (int64_t)(c0 + c) * a.M + ix.w) : make_float2(0.f, 0.f);
-            s_e[my_slot] = e;
-            atomicAdd(&s_cnt[e], 1);
+            atomicAdd(&s_cnt[my_row], 1);
         }
     }
     __syncthreads();
-    // exclusive scan of the bin counts (NE is at most a few thousand): each thread a chunk
+    // exclusive scan of the row counts: each thread a chunk, then a block scan of the chunk sums
     {
         __shared__ int s_part[512];
-        const int per = (NE + nt - 1) / nt;
-        const int b0 = min(NE, tid * per), b1 = min(NE, b0 + per);
+        const int per = (NR + nt - 1) / nt;
+        const int b0 = min(NR, tid * per), b1 = min(NR, b0 + per);
         int sum = 0;
         for (int b = b0; b < b1; ++b) sum += s_cnt[b];
         s_part[tid] = sum;
@@ -373,14 +375,16 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
             s_cnt[b] = run;
             run += c;
         }
-        if (tid == nt - 1) s_cnt[NE] = run;
+        if (tid == nt - 1) s_cnt[NR] = run;
     }
     __syncthreads();
-    // place hits: s_cnt[e] becomes the cursor of bin e (its end once all are placed)
-    if (my_slot >= 0) s_list[atomicAdd(&s_cnt[my_e], 1)] = my_slot;
+    // place hits: s_cnt[r] becomes the cursor of row r (its end once all are placed)
+    if (my_slot >= 0) s_list[atomicAdd(&s_cnt[my_row], 1)] = my_slot;
     __syncthreads();
 
-    // gather: thread t owns cell t (the block has one thread per tile cell)
+    // gather: thread t owns cell t (one thread per tile cell).  The points covering cell l
+    // start in rows l_0 .. l_0 + J - 1 (and l_1 .. l_1 + J - 1 in 3-D) and have
+    // e_last - l_last in [0, J); tap j_d = J - 1 - (e_d - l_d).
     const int tcells = Bt[0] * Bt[1] * Bt[2];
     const int cell = tid;
     float2 acc[CPT];
@@ -395,30 +399,25 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
                 r /= Bt[d];
             }
         }
-        // loops kept rolled: one copy of the pair loop keeps the code small
+        const int ll = l[D - 1];
 #pragma unroll 1
         for (int a0 = 0; a0 < J; ++a0) {
-            const int e0 = l[0] + a0;            // tap j0 = J - 1 - a0
 #pragma unroll 1
-            for (int a1 = 0; a1 < (D > 1 ? J : 1); ++a1) {
-                const int e1 = D > 1 ? l[1] + a1 : 0;
-#pragma unroll 1
-                for (int a2 = 0; a2 < (D > 2 ? J : 1); ++a2) {
-                    const int e2 = D > 2 ? l[2] + a2 : 0;
-                    const int e = (e0 * E[1] + e1) * E[2] + e2;
-                    const int h0 = e ? s_cnt[e - 1] : 0, h1 = s_cnt[e];   // cursors now mark bin ends
-                    for (int hh = h0; hh < h1; ++hh) {
-                        const int h = s_list[hh];
-                        const float* w = s_w + h * (D * J);
-                        float wt = w[J - 1 - a0];
-                        if (D > 1) wt *= w[J + J - 1 - a1];
-                        if (D > 2) wt *= w[2 * J + J - 1 - a2];
-                        const float2* yv = s_y + (size_t)h * (CPT + 1);
+            for (int a1 = 0; a1 < (D > 2 ? J : 1); ++a1) {
+                const int row = D == 2 ? l[0] + a0 : (l[0] + a0) * E[1] + (l[1] + a1);
+                const int h0 = row ? s_cnt[row - 1] : 0, h1 = s_cnt[row];   // cursors now mark row ends
+                for (int hh = h0; hh < h1; ++hh) {
+                    const int h = s_list[hh];
+                    const int al = s_el[h] - ll;
+                    if (al < 0 || al >= J) continue;
+                    const float* w = s_w + h * (D * J);
+                    float wt = w[J - 1 - a0] * w[(D - 1) * J + J - 1 - al];
+                    if (D > 2) wt *= w[J + J - 1 - a1];
+                    const float2* yv = s_y + (size_t)h * (CPT + 1);
 #pragma unroll
-                        for (int c = 0; c < CPT; ++c) {
-                            acc[c].x = fmaf(wt, yv[c].x, acc[c].x);
-                            acc[c].y = fmaf(wt, yv[c].y, acc[c].y);
-                        }
+                    for (int c = 0; c < CPT; ++c) {
+                        acc[c].x = fmaf(wt, yv[c].x, acc[c].x);
+                        acc[c].y = fmaf(wt, yv[c].y, acc[c].y);
                     }
                 }
             }
@@ -455,8 +454,8 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
 template <int D, int J>
 static cudaError_t spread_cells_cpt(const SpreadArgs& a, cudaStream_t s, int threads) {
     const int cpt = a.CC;
-    int E = 1;
-    for (int d = 0; d < D; ++d) E *= a.B[d] + J - 1;
+    int E = 1;   // row bins
+    for (int d = 0; d < D - 1; ++d) E *= a.B[d] + J - 1;
     const size_t smem = (size_t)a.P * D * J * sizeof(float) + sizeof(float) + (size_t)a.P * (cpt + 1) * sizeof(float2) +
                         2 * (size_t)a.P * sizeof(int) + (size_t)(E + 1) * sizeof(int);
     dim3 grid((unsigned)a.max_items, (unsigned)((a.C + cpt - 1) / cpt));
