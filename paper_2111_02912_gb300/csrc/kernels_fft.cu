@@ -142,38 +142,35 @@ struct Dft<16, DIR> {
     }
 };
 
-// Global side of a fused first / last stage: tile line (lb, ls) is line
-// (b0 + lb, s0 + ls) of a [B][n][S] array; position p of the transform holds
-// element e(p) of the line (zero padding / crop: e = (p + n/2) mod L when p is
-// one of the n kept positions).
+// Global side of a fused first / last stage, for the one tile line a thread
+// works on (the block size is a multiple of the tile's line count, so butterfly
+// u = tid + k * blockDim always falls on line tid mod TL).  Position p of the
+// transform holds element e(p) of the line (zero padding / crop: e = (p + n/2)
+// mod L when p is one of the n kept positions); elements are S apart.
 struct LineIO {
-    const float2* in;
-    float2* out;
-    int64_t B, S, b0, s0;
-    int L, n_in, n_out, TS, lgTS;
-    bool pruned_in, cropped_out;
+    const float2* in_line;   // element 0 of the thread's input line
+    float2* out_line;        // element 0 of the thread's output line
+    int64_t S;
+    int L, n_in, n_out;
+    bool valid, pruned_in, cropped_out;
 
-    __device__ __forceinline__ float2 load(int line, int p) const {
-        const int lb = line >> lgTS, ls = line & (TS - 1);
-        const int64_t b = b0 + lb, s = s0 + ls;
+    __device__ __forceinline__ float2 load(int p) const {
         int e = p;
         if (pruned_in) {
             const int h = n_in >> 1;
             e = p < h ? p + h : (p >= L - h ? p - (L - h) : -1);
         }
-        if (e < 0 || b >= B || s >= S) return make_float2(0.f, 0.f);
-        return in[(b * n_in + e) * S + s];
+        if (e < 0 || !valid) return make_float2(0.f, 0.f);
+        return in_line[e * S];
     }
-    __device__ __forceinline__ void store(int line, int p, float2 v) const {
-        const int lb = line >> lgTS, ls = line & (TS - 1);
-        const int64_t b = b0 + lb, s = s0 + ls;
+    __device__ __forceinline__ void store(int p, float2 v) const {
         int e = p;
         if (cropped_out) {
             const int h = n_out >> 1;
             e = p < h ? p + h : (p >= L - h ? p - (L - h) : -1);
         }
-        if (e < 0 || b >= B || s >= S) return;
-        out[(b * n_out + e) * S + s] = v;
+        if (e < 0 || !valid) return;
+        out_line[e * S] = v;
     }
 };
 
@@ -201,7 +198,7 @@ __device__ __forceinline__ void fft_stage(const float2* __restrict__ src, float2
             for (int r = 0; r < R; ++r) v[r] = sp[r * sstride];
         } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = io.load(line, j + r * LR);
+            for (int r = 0; r < R; ++r) v[r] = io.load(j + r * LR);
         }
         if (st.Ns > 1) {
             const int tstep = kk * st.tw_step;
@@ -220,7 +217,7 @@ __device__ __forceinline__ void fft_stage(const float2* __restrict__ src, float2
             for (int r = 0; r < R; ++r) dp[r * dstride] = v[r];
         } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) io.store(line, d0 + r * st.Ns, v[r]);
+            for (int r = 0; r < R; ++r) io.store(d0 + r * st.Ns, v[r]);
         }
     }
     __syncthreads();
@@ -323,19 +320,19 @@ __global__ void __launch_bounds__(256) k_line_fft(LinePass a) {
     for (int chunk = 0; chunk < nchunks; ++chunk) {
         const int64_t s0 = ((int64_t)blockIdx.y * nchunks + chunk) * TS;
         LineIO io;
-        io.in = a.in;
-        io.out = a.out;
-        io.B = a.B;
-        io.S = a.S;
-        io.b0 = b0;
-        io.s0 = s0;
-        io.L = L;
-        io.n_in = a.n_in;
-        io.n_out = a.n_out;
-        io.TS = TS;
-        io.lgTS = a.lgTS;
-        io.pruned_in = DIR < 0;
-        io.cropped_out = DIR > 0;
+        {
+            const int line = tid & (TL - 1);
+            const int64_t b = b0 + (line >> a.lgTS), sl = s0 + (line & (TS - 1));
+            io.valid = b < a.B && sl < a.S;
+            io.in_line = a.in + (io.valid ? b * a.n_in * a.S + sl : 0);
+            io.out_line = a.out + (io.valid ? b * a.n_out * a.S + sl : 0);
+            io.S = a.S;
+            io.L = L;
+            io.n_in = a.n_in;
+            io.n_out = a.n_out;
+            io.pruned_in = DIR < 0;
+            io.cropped_out = DIR > 0;
+        }
         // ---------------- prologue: the first pass builds the tile from the image
         const int nfill = KIND == PASS_FWD_FIRST ? L * TL : 0;
         for (int f = tid; f < nfill; f += nt) {
