@@ -98,3 +98,43 @@ def adjoint_vjp_omega(op, g, y, smaps=None):
             t = np.conj(op.forward(gc * _r_weight(op.shape, d)))   # sum_j conj(w_j) e^{+i omega.r_j}
             out[d] += np.real(1j * y[c] * t)
     return out
+
+
+def gram_vjp_omega(op, x, g, smaps=None):
+    """d/d omega of Re<g, E' E x>, from the Gram Jacobian of Sec. II-E, Eq. (e,A'A,x,omd).
+
+    [dE'E/d omega_1 ... dE'E/d omega_M] x = -i E' diag{E(x . r^[d])} + i diag{r^[d]} E' diag{E x}
+    (A -> E by Sec. II-G).  Column (c, l) of E' diag{w} contracted with g^H is
+    conj([E g]_cl) w_cl, and of diag{r} E' diag{w} is conj([E(g . r)]_cl) w_cl;
+    omega_l enters every coil's column l, so coils are summed.  Returns (D, M)."""
+    D = len(op.shape)
+    Ex = sense_forward(op, x, smaps)
+    Eg = sense_forward(op, g, smaps)
+    out = np.zeros((D, op.omega.shape[1]))
+    for d in range(D):
+        rw = _r_weight(op.shape, d)
+        Exr = sense_forward(op, np.asarray(x) * rw, smaps)
+        Egr = sense_forward(op, np.asarray(g) * rw, smaps)
+        term = -1j * np.conj(Eg) * Exr + 1j * np.conj(Egr) * Ex
+        out[d] = np.sum(np.real(term), axis=0)
+    return out
+
+
+def dense_sense_matrix(op_matrix, smaps):
+    """Stack [A diag(s_1); ...; A diag(s_C)] for a dense single-coil A (tiny sizes)."""
+    S = np.asarray(smaps, dtype=np.complex128).reshape(len(smaps), -1)
+    return np.concatenate([op_matrix * S[c][None, :] for c in range(S.shape[0])], axis=0)
+
+
+def psd_inverse_vjp(op, E_dense, b, g, smaps=None, lam=1e-2):
+    """z = F^-1 b, F = E'E + lam I, and the VJPs of Re<g, z> (Sec. II-F, Eq. (e,inv,omd)).
+
+    Eq. (e,inv,omd): D_omega F^-1 b = -F^-1 (D_omega F z), z = F^-1 b, so with
+    u = F^-1 g (F Hermitian): grad_b = u and grad_omega = -gram_vjp(x = z, g = u).
+    F is solved densely here (tiny sizes).  Returns (z, grad_b, grad_omega)."""
+    shape = op.shape
+    N = int(np.prod(shape))
+    F = E_dense.conj().T @ E_dense + lam * np.eye(N)
+    z = np.linalg.solve(F, np.asarray(b, dtype=np.complex128).ravel()).reshape(shape)
+    u = np.linalg.solve(F, np.asarray(g, dtype=np.complex128).ravel()).reshape(shape)
+    return z, u, -gram_vjp_omega(op, z, u, smaps)

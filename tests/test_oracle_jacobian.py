@@ -101,3 +101,55 @@ def test_nufft_jacobians_close_to_exact(shape):
     gn, gxn = jb.vjp_omega_x(KBNufft(shape, om), x, v, S)
     assert np.linalg.norm(gn - ge) / np.linalg.norm(ge) < 1e-4
     assert np.linalg.norm(gxn - gxe) / np.linalg.norm(gxe) < 1e-4
+
+
+def test_gram_vjp_matches_finite_differences():
+    """Eq. (e,A'A,x,omd) contracted with g equals d/d omega Re<g, E'E x> (SENSE, exact NUDFT)."""
+    shape = (6, 8)
+    g, om, x, S, _ = _case(shape, M=7, C=2)
+    gimg = g.standard_normal(shape) + 1j * g.standard_normal(shape)
+    a = jb.gram_vjp_omega(NUDFT(shape, om), x, gimg, S)
+
+    def f(o):
+        op = NUDFT(shape, o)
+        return np.real(np.vdot(gimg, jb.sense_adjoint(op, jb.sense_forward(op, x, S), S)))
+    h = 1e-6
+    for d in range(2):
+        for i in range(om.shape[1]):
+            e = np.zeros_like(om)
+            e[d, i] = h
+            assert abs((f(om + e) - f(om - e)) / (2 * h) - a[d, i]) < 1e-7 * np.abs(a).max()
+
+
+def test_psd_inverse_vjp_matches_finite_differences():
+    """Eq. (e,inv,omd): gradients of Re<g, (E'E + lam I)^-1 b> w.r.t. omega and b (dense solves)."""
+    from oracle.nudft import nudft_matrix
+    shape, lam = (4, 6), 0.3
+    g, om, x, S, _ = _case(shape, M=9, C=2)
+    b = x
+    gimg = g.standard_normal(shape) + 1j * g.standard_normal(shape)
+
+    def solve(o):
+        E = jb.dense_sense_matrix(nudft_matrix(shape, o), S)
+        F = E.conj().T @ E + lam * np.eye(E.shape[1])
+        return np.linalg.solve(F, b.ravel()).reshape(shape)
+
+    E = jb.dense_sense_matrix(nudft_matrix(shape, om), S)
+    z, gb, go = jb.psd_inverse_vjp(NUDFT(shape, om), E, b, gimg, S, lam)
+    assert np.allclose(z, solve(om), atol=1e-12)
+    h = 1e-6
+    for d in range(2):
+        for i in range(om.shape[1]):
+            e = np.zeros_like(om)
+            e[d, i] = h
+            fd = (np.real(np.vdot(gimg, solve(om + e))) - np.real(np.vdot(gimg, solve(om - e)))) / (2 * h)
+            assert abs(fd - go[d, i]) < 1e-6 * max(1.0, np.abs(go).max())
+    # grad_b: L = Re<g, F^-1 b> is linear in b with gradient F^-1 g (F Hermitian)
+    for j in [(0, 0), (2, 3)]:
+        e = np.zeros(shape, complex)
+        e[j] = h
+        F = E.conj().T @ E + lam * np.eye(E.shape[1])
+        f = lambda bb: np.real(np.vdot(gimg, np.linalg.solve(F, bb.ravel())))
+        dre = (f(b + e) - f(b - e)) / (2 * h)
+        dim = (f(b + 1j * e) - f(b - 1j * e)) / (2 * h)
+        assert abs((dre + 1j * dim) - gb[j]) < 1e-7 * np.abs(gb).max()
