@@ -102,6 +102,7 @@ struct LinePass {
     int64_t B, S;          // outer lines, inner stride (complex elements)
     int TB, TS, lgTS, lgTL, TLP;
     int nchunks;           // coil-sum epilogue: channel chunks looped in one block
+    int64_t ntiles_s;      // channel tiles per row tile (the grid is flat: ntiles_b * ntiles_s blocks)
     int coil_sum;
     const float2* in;
     float2* out;

@@ -290,7 +290,10 @@ __global__ void __launch_bounds__(256) k_line_fft(LinePass a) {
     float* row_r = row_scale + TB;                        // [TB][2]
     __shared__ FftStage sst[kMaxStages];
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int64_t b0 = (int64_t)blockIdx.x * TB;
+    // flat grid: block = (row tile, channel tile), channel tiles fastest
+    const int64_t bid = blockIdx.x;
+    const int64_t by = bid % a.ntiles_s;
+    const int64_t b0 = (bid / a.ntiles_s) * TB;
 
     for (int i = tid; i < L; i += nt) tw[i] = a.ax.tw[i];
     if (tid == 0) {
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(256) k_line_fft(LinePass a) {
     const int nchunks = a.nchunks;
 
     for (int chunk = 0; chunk < nchunks; ++chunk) {
-        const int64_t s0 = ((int64_t)blockIdx.y * nchunks + chunk) * TS;
+        const int64_t s0 = (by * nchunks + chunk) * TS;
         LineIO io;
         {
             const int line = tid & (TL - 1);
@@ -398,7 +401,7 @@ __global__ void __launch_bounds__(256) k_line_fft(LinePass a) {
         __syncthreads();
     }
     if (KIND == PASS_INV_LAST && a.coil_sum) {
-        float2* xo = a.im.xout + (int64_t)blockIdx.y * a.im.xout_stride;
+        float2* xo = a.im.xout + by * a.im.xout_stride;
         for (int f = tid; f < TB * a.n_out; f += nt) {
             const int lb = f / a.n_out, e = f - lb * a.n_out;
             const int64_t b = b0 + lb;

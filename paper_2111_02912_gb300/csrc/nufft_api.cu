@@ -427,7 +427,8 @@ int forward_grids(nufft_plan_s* p, int C, int nd, int has_plain, const float2* x
         a.im = im;
         a.magic_L = magic_of((uint32_t)L);
         a.magic_n = magic_of((uint32_t)a.n_out);
-        dim3 grid((unsigned)((B + t.TB - 1) / t.TB), (unsigned)((S + t.TS - 1) / t.TS));
+        a.ntiles_s = (S + t.TS - 1) / t.TS;
+        dim3 grid((unsigned)(((B + t.TB - 1) / t.TB) * a.ntiles_s));
         const PassKind kind = (k == 0) ? PASS_FWD_FIRST : PASS_FWD_MID;
         int st = launch(p, k == 0 ? PK_FFT_FWD_FIRST : PK_FFT_FWD_MID, s,
                         [&] { return launch_line_pass(kind, a, grid, t.threads, t.smem, s); });
@@ -514,7 +515,8 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
         }
         a.magic_L = magic_of((uint32_t)L);
         a.magic_n = magic_of((uint32_t)a.n_out);
-        dim3 grid((unsigned)((B + t.TB - 1) / t.TB), (unsigned)chunks);
+        a.ntiles_s = chunks;
+        dim3 grid((unsigned)(((B + t.TB - 1) / t.TB) * chunks));
         const PassKind kind = last ? PASS_INV_LAST : PASS_INV_MID;
         st = launch(p, last ? PK_FFT_INV_LAST : PK_FFT_INV_MID, s,
                     [&] { return launch_line_pass(kind, a, grid, t.threads, t.smem, s); });
