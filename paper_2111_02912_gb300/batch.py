@@ -1,0 +1,135 @@
+"""Many independent problems of uneven shape: autotuned plans, one CUDA graph per batch.
+
+Each problem (image size, trajectory, coil count) gets its own plan.  One
+"Jacobian step" per problem is nufft_set_points + nufft_forward + nufft_vjp_omega_x
+(y, grad_omega, grad_x), the hot path of the 2-D radial case.  Two ways to run
+a batch:
+
+* plain: the problems' calls one after another on the current stream;
+* graph: every problem's calls recorded once into a CUDA graph, the problems
+  dealt round-robin to several streams so that independent problems overlap;
+  a step is then one graph launch.
+
+The autotuner picks each problem's spread tile shape (bin_size) by timing one
+step per candidate on the device, cached per (shape, coils, log2 M) class.
+"""
+import math
+
+import torch
+
+from .plan import Plan
+
+BIN_CANDIDATES_2D = ((16, 16), (16, 32), (32, 16), (8, 32))
+
+
+class Autotuner:
+    def __init__(self, candidates=BIN_CANDIDATES_2D, reps=3):
+        self.candidates = tuple(candidates)
+        self.reps = reps
+        self.cache = {}
+
+    @staticmethod
+    def key(shape, C, M):
+        return (tuple(shape), 1 << max(0, int(C) - 1).bit_length(), int(math.log2(max(M, 1))))
+
+    def choose(self, item):
+        k = self.key(item.shape, item.C, item.M)
+        if k in self.cache:
+            return self.cache[k]
+        best, best_ms = None, float("inf")
+        for b in self.candidates:
+            if any(bd > n * 2 for bd, n in zip(b, item.shape)):
+                continue
+            plan = Plan(item.shape, item.om, max_coils=item.C, bin_size=b)
+            run = lambda: _step(plan, item)
+            run()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(self.reps):
+                run()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / self.reps
+            if ms < best_ms:
+                best, best_ms = b, ms
+            del plan
+        self.cache[k] = best
+        return best
+
+
+class _Item:
+    def __init__(self, p, device):
+        t = lambda a: torch.from_numpy(a).to(device)
+        self.shape = tuple(p["shape"])
+        self.C = int(p["C"])
+        self.om, self.x, self.v = t(p["omega"]), t(p["x"]), t(p["v"])
+        self.S = t(p["smaps"]) if p.get("smaps") is not None else None
+        self.M = int(self.om.shape[1])
+        self.y = torch.empty((self.C, self.M), dtype=torch.complex64, device=device)
+        self.go = torch.empty((len(self.shape), self.M), dtype=torch.float32, device=device)
+        self.gx = torch.empty(self.shape if self.S is not None else (self.C,) + self.shape,
+                              dtype=torch.complex64, device=device)
+        self.plan = None
+        self.bin_size = None
+
+
+def _step(plan, it):
+    plan.set_points(it.om)
+    plan.forward(it.x, it.S, out=it.y)
+    plan.vjp_omega_x(it.x, it.v, it.S, out=(it.go, it.gx))
+
+
+class BatchedJacobian:
+    """A batch of independent problems; see the module docstring."""
+
+    def __init__(self, problems, device="cuda", streams=4, autotune=True, tuner=None):
+        self.device = torch.device(device)
+        self.items = [_Item(p, self.device) for p in problems]
+        self.tuner = tuner if tuner is not None else (Autotuner() if autotune else None)
+        for it in self.items:
+            it.bin_size = self.tuner.choose(it) if self.tuner is not None else None
+            it.plan = Plan(it.shape, it.om, max_coils=it.C, bin_size=it.bin_size)
+        self.nstreams = max(1, int(streams))
+        self.graph = None
+
+    def units(self):
+        """NU-points x channels of one batch step: M C (1 + D) per problem."""
+        return sum(it.M * it.C * (1 + len(it.shape)) for it in self.items)
+
+    def run_plain(self):
+        for it in self.items:
+            _step(it.plan, it)
+
+    def capture(self):
+        streams = [torch.cuda.Stream(device=self.device) for _ in range(self.nstreams)]
+        main = torch.cuda.current_stream(self.device)
+        # warm-up on the side streams (first launches set kernel attributes outside the capture)
+        for i, it in enumerate(self.items):
+            s = streams[i % self.nstreams]
+            s.wait_stream(main)
+            with torch.cuda.stream(s):
+                _step(it.plan, it)
+        for s in streams:
+            main.wait_stream(s)
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            cap = torch.cuda.current_stream(self.device)
+            for s in streams:
+                s.wait_stream(cap)
+            for i, it in enumerate(self.items):
+                with torch.cuda.stream(streams[i % self.nstreams]):
+                    _step(it.plan, it)
+            for s in streams:
+                cap.wait_stream(s)
+        self.graph = g
+        self._streams = streams
+        return g
+
+    def replay(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+    def outputs(self):
+        return [(it.y, it.go, it.gx) for it in self.items]

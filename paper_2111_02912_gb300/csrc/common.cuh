@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace nj {
 
 constexpr int kMaxDim = 3;
@@ -68,5 +70,19 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// Raise a kernel's dynamic shared-memory limit once per device (not on every
+// launch), so that launches recorded into a CUDA graph make no attribute call.
+template <auto KERNEL>
+inline void ensure_smem(size_t bytes) {
+    static std::atomic<size_t> done[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (bytes > done[dev].load(std::memory_order_relaxed)) {
+        cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        done[dev].store(bytes, std::memory_order_relaxed);
+    }
+}
 
 }  // namespace nj

@@ -429,19 +429,19 @@ cudaError_t launch_line_pass(PassKind kind, const LinePass& a, dim3 grid, int th
                              cudaStream_t s) {
     switch (kind) {
         case PASS_FWD_FIRST:
-            cudaFuncSetAttribute(k_line_fft<PASS_FWD_FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            ensure_smem<k_line_fft<PASS_FWD_FIRST>>(smem);
             k_line_fft<PASS_FWD_FIRST><<<grid, threads, smem, s>>>(a);
             break;
         case PASS_FWD_MID:
-            cudaFuncSetAttribute(k_line_fft<PASS_FWD_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            ensure_smem<k_line_fft<PASS_FWD_MID>>(smem);
             k_line_fft<PASS_FWD_MID><<<grid, threads, smem, s>>>(a);
             break;
         case PASS_INV_MID:
-            cudaFuncSetAttribute(k_line_fft<PASS_INV_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            ensure_smem<k_line_fft<PASS_INV_MID>>(smem);
             k_line_fft<PASS_INV_MID><<<grid, threads, smem, s>>>(a);
             break;
         case PASS_INV_LAST:
-            cudaFuncSetAttribute(k_line_fft<PASS_INV_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            ensure_smem<k_line_fft<PASS_INV_LAST>>(smem);
             k_line_fft<PASS_INV_LAST><<<grid, threads, smem, s>>>(a);
             break;
     }

@@ -460,13 +460,13 @@ static cudaError_t spread_cells_cpt(const SpreadArgs& a, cudaStream_t s, int thr
                         2 * (size_t)a.P * sizeof(int) + (size_t)(E + 1) * sizeof(int);
     dim3 grid((unsigned)a.max_items, (unsigned)((a.C + cpt - 1) / cpt));
     if (cpt <= 4) {
-        cudaFuncSetAttribute(k_spread_cells<D, J, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ensure_smem<k_spread_cells<D, J, 4>>(smem);
         k_spread_cells<D, J, 4><<<grid, threads, smem, s>>>(a);
     } else if (cpt <= 8) {
-        cudaFuncSetAttribute(k_spread_cells<D, J, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ensure_smem<k_spread_cells<D, J, 8>>(smem);
         k_spread_cells<D, J, 8><<<grid, threads, smem, s>>>(a);
     } else {
-        cudaFuncSetAttribute(k_spread_cells<D, J, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ensure_smem<k_spread_cells<D, J, 16>>(smem);
         k_spread_cells<D, J, 16><<<grid, threads, smem, s>>>(a);
     }
     return cudaGetLastError();
@@ -515,7 +515,7 @@ __global__ void k_zero_heavy_tiles(SpreadArgs a) {
 
 template <int D, int J>
 static cudaError_t spread_j(const SpreadArgs& a, cudaStream_t s, size_t smem, dim3 grid) {
-    cudaFuncSetAttribute(k_spread<D, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ensure_smem<k_spread<D, J>>(smem);
     k_spread<D, J><<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
 }

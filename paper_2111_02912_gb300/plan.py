@@ -94,10 +94,13 @@ class Plan:
                              _ptr(dy, torch.complex64, "dy"), _ptr(y, torch.complex64, "y"), _stream())
         return (dy, y) if want_y else dy
 
-    def vjp_omega_x(self, x, v, smaps=None, need_omega=True, need_x=True):
+    def vjp_omega_x(self, x, v, smaps=None, need_omega=True, need_x=True, out=None):
         C = int(v.shape[0])
-        go = torch.empty((self.D, self.M), dtype=torch.float32, device=v.device) if need_omega else None
-        gx = torch.empty(self._img_shape(C, smaps), dtype=torch.complex64, device=v.device) if need_x else None
+        if out is not None:
+            go, gx = out
+        else:
+            go = torch.empty((self.D, self.M), dtype=torch.float32, device=v.device) if need_omega else None
+            gx = torch.empty(self._img_shape(C, smaps), dtype=torch.complex64, device=v.device) if need_x else None
         _abi.nufft_vjp_omega_x(self.handle, C, _ptr(x, torch.complex64, "x"),
                                _ptr(smaps, torch.complex64, "smaps", (C,) + self.shape),
                                _ptr(v, torch.complex64, "v", (C, self.M)),

@@ -134,3 +134,24 @@ def workload(name, scale=1.0):
         om = np.stack([kr * math.cos(th), kr * math.sin(th)]).astype(np.float32)
         return dict(shape=shape, x=x, smaps=gaussian_bump_maps(shape, 8), omega=om, C=8)
     raise KeyError(name)
+
+
+def batched_problems(n=64, seed_index=4, sides=(64, 128, 192, 256, 320, 384), m_range=(4000, 200000),
+                     coil_range=(1, 32)):
+    """n independent 2-D problems of uneven size: side uniform over `sides`, M uniform over
+    m_range, random-angle radial spokes of 2N samples (the last one truncated), coils uniform
+    over coil_range; images i.i.d. N(0,1), Gaussian-bump maps, incoming gradients v i.i.d."""
+    g = rng(seed_index)
+    out = []
+    for _ in range(n):
+        N = int(g.choice(sides))
+        M = int(g.integers(m_range[0], m_range[1] + 1))
+        C = int(g.integers(coil_range[0], coil_range[1] + 1))
+        n_read = 2 * N
+        n_spokes = -(-M // n_read)
+        om = radial_2d(n_spokes, n_read, golden=False, g=g)[:, :M]
+        shape = (N, N)
+        v = ((g.standard_normal((C, M)) + 1j * g.standard_normal((C, M))) / math.sqrt(2)).astype(np.complex64)
+        out.append(dict(shape=shape, x=random_image(g, shape), smaps=gaussian_bump_maps(shape, C),
+                        omega=np.ascontiguousarray(om), v=v, C=C))
+    return out
