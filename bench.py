@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="radial320", choices=["radial320", "cgsense3d", "batched"],
+    ap.add_argument("--workload", default="radial320", choices=["radial320", "cgsense3d", "batched", "serving"],
                     help="radial320: the hot-path step (default); cgsense3d: gradient of an unrolled "
                          "CG-SENSE loss on the 3-D radial workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -499,8 +499,74 @@ def run_batched(args):
         print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ serving
+def run_serving(args, rate=200.0, seconds=3.0):
+    import torch
+
+    from paper_2111_02912_gb300.serve import Request, Server, latency_summary
+    from paper_2111_02912_gb300.workloads import batched_problems
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    probs = batched_problems(64)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    pool = [dict(shape=p["shape"], om=t(p["omega"]), S=t(p["smaps"]), x=t(p["x"]), y=t(p["v"]), C=p["C"],
+                 M=p["omega"].shape[1]) for p in probs]
+    g = np.random.default_rng(2111_02912 + 5)
+    n_req = int(rate * seconds)
+    arrivals = np.cumsum(g.exponential(1.0 / rate, n_req))
+    picks = g.integers(0, len(pool), n_req)
+    kinds = np.where(g.random(n_req) < 0.5, "recon", "traj_grad")
+
+    def make(i, j, kind):
+        q = pool[j]
+        return Request(i, kind, q["shape"], q["om"], q["S"], x=q["x"], y=q["y"], lam=1e-3, iters=15)
+
+    srv = Server(budget_bytes=120 << 30, slots=8, device=dev)
+    for j in range(len(pool)):                  # warm-up: resident plans for every problem class
+        srv.submit(make(-1, j, "recon"))
+    srv.drain()
+    srv.done.clear()
+
+    def units(r, q):
+        D = 2
+        return q["M"] * q["C"] * (31 if r.kind == "recon" else 1 + D)
+
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        k = 0
+        while k < n_req or srv.pending or srv.running:
+            now = time.perf_counter() - t0
+            while k < n_req and arrivals[k] <= now:
+                srv.submit(make(k, picks[k], kinds[k]), now=t0 + arrivals[k])
+                k += 1
+            srv.poll()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    done = srv.done
+    tot_units = sum(units(r, pool[picks[r.rid]]) for r in done)
+    lat = latency_summary(done)
+    line = {"metric": METRIC, "value": tot_units / wall, "unit": UNIT, "n_gpus": ws, "steps": len(done),
+            "warmup": len(pool), "ms_per_step": 1e3 * wall / len(done), "p50_ms": lat["p50_ms"],
+            "p99_ms": lat["p99_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 (fp32 complex)", "data": "synthetic (seeded uneven radial problems, Poisson arrivals)",
+            "config": {"workload": "serving: Poisson arrivals at %.0f req/s for %.1f s; each request picks one of "
+                                   "64 uneven 2-D problems (sides 64-384, M 4k-200k, coils 1-32) and is a CG-SENSE "
+                                   "reconstruction (15 iterations of E'E + 1e-3 I) or a trajectory gradient of "
+                                   "||E x - y||^2 (50/50); 8 slots (streams), 120 GiB admission budget, resident "
+                                   "plans" % (rate, seconds),
+                       "requests": len(done), "requests_per_s": len(done) / wall, "wall_s": wall,
+                       "latency_mean_ms": lat["mean_ms"], "l2": "inputs larger than L2"},
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 if __name__ == "__main__":
     a = parse()
+    if a.workload == "serving" and a.impl != "reference":
+        run_serving(a)
+        sys.exit(0)
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "cgsense3d":

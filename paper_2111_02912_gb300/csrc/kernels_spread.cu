@@ -267,8 +267,10 @@ __global__ void __launch_bounds__(256, 2) k_spread(SpreadArgs a) {
 // e_d in [l_d, l_d + J - 1] for every axis, with tap j_d = l_d + J - 1 - e_d,
 // so it visits the J (2-D) or J^2 (3-D) rows around it, keeps the points whose
 // last coordinate fits, and sums w * y in registers.  No atomics on the tile;
-// within a row the points are summed in the order they were placed
-// (rounding-level differences between runs).
+// within a row the points are summed in original-index order, so a tile that
+// is one work item is bitwise reproducible.  Heavy tiles (several work items)
+// are cleared first and receive float2 vector atomics (rounding-level order
+// differences).
 template <int D, int J, int CPT>
 __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
     extern __shared__ float4 smem4[];
@@ -297,11 +299,14 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
     const int P = a.P;
     const int c0 = blockIdx.y * CPT;
     const int ncc = min(CPT, a.C - c0);
-    // shared layout: weights [P][D*J], y [P][CPT+1], last start coordinate [P], sorted hits [P], row cursors [NR+1]
+    // shared layout: weights [P][D*J], y [P][CPT+1], last start coordinate, row and original index
+    // per hit [P] each, sorted hits [P], row cursors [NR+1]
     float* s_w = (float*)smem4;
     float2* s_y = (float2*)(s_w + P * D * J + ((P * D * J) & 1));
     int* s_el = (int*)(s_y + (size_t)P * (CPT + 1));
-    int* s_list = s_el + P;
+    int* s_row = s_el + P;
+    int* s_orig = s_row + P;
+    int* s_list = s_orig + P;
     int* s_cnt = s_list + P;
 
     if (tid < kKbTerms) coef[tid] = a.kb.a[tid];
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
     const int nn = s_nn;
     const int lo = part * P, hi = min(s_pref[nn], lo + P);
     const int cand = lo + tid;
-    int my_row = -1, my_slot = -1;
+    int my_row = -1, my_slot = -1, my_orig = 0;
     if (tid < P && cand < hi) {
         int q = 0;
         while (q + 1 < nn && s_pref[q + 1] <= cand) ++q;
@@ -337,7 +342,10 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
         if (hit) {
             my_slot = atomicAdd(&s_nh, 1);
             my_row = D == 2 ? e[0] : e[0] * E[1] + e[1];
+            my_orig = ix.w;
             s_el[my_slot] = e[D - 1];
+            s_row[my_slot] = my_row;
+            s_orig[my_slot] = my_orig;
             const float4 fr = a.pts.frac[p];
             float* w = s_w + my_slot * (D * J);
 #pragma unroll
@@ -378,8 +386,16 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
         if (tid == nt - 1) s_cnt[NR] = run;
     }
     __syncthreads();
-    // place hits: s_cnt[r] becomes the cursor of row r (its end once all are placed)
-    if (my_slot >= 0) s_list[atomicAdd(&s_cnt[my_row], 1)] = my_slot;
+    // place hits in a fixed order: within a row by original point index, so the sums below
+    // do not depend on the order in which threads arrived.  s_cnt[r] then marks the end of row r.
+    if (my_slot >= 0) {
+        const int nh = s_nh;
+        int rank = 0;
+        for (int h = 0; h < nh; ++h) rank += s_row[h] == my_row && s_orig[h] < my_orig;
+        s_list[s_cnt[my_row] + rank] = my_slot;
+    }
+    __syncthreads();
+    if (my_slot >= 0) atomicAdd(&s_cnt[my_row], 1);   // start -> end of the row (order-free)
     __syncthreads();
 
     // gather: thread t owns cell t (one thread per tile cell).  The points covering cell l
@@ -457,7 +473,7 @@ static cudaError_t spread_cells_cpt(const SpreadArgs& a, cudaStream_t s, int thr
     int E = 1;   // row bins
     for (int d = 0; d < D - 1; ++d) E *= a.B[d] + J - 1;
     const size_t smem = (size_t)a.P * D * J * sizeof(float) + sizeof(float) + (size_t)a.P * (cpt + 1) * sizeof(float2) +
-                        2 * (size_t)a.P * sizeof(int) + (size_t)(E + 1) * sizeof(int);
+                        4 * (size_t)a.P * sizeof(int) + (size_t)(E + 1) * sizeof(int);
     dim3 grid((unsigned)a.max_items, (unsigned)((a.C + cpt - 1) / cpt));
     if (cpt <= 4) {
         ensure_smem<k_spread_cells<D, J, 4>>(smem);

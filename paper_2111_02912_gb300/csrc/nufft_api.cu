@@ -285,7 +285,8 @@ size_t max_items(const nufft_plan_s& p, int64_t cap) {
 }
 
 size_t point_bytes(const nufft_plan_s& p, int64_t cap) {
-    return (size_t)cap * (2 * sizeof(int) + sizeof(int4) + sizeof(float4)) + max_items(p, cap) * sizeof(int4);
+    size_t b = (size_t)cap * (2 * sizeof(int) + sizeof(int4) + sizeof(float4)) + max_items(p, cap) * sizeof(int4);
+    return b;
 }
 
 int alloc_points(nufft_plan_s* p, int64_t cap) {

@@ -191,7 +191,7 @@ def test_gather_is_deterministic_and_resort_is_consistent():
     g2, x2 = plan.vjp_omega_x(X, V, S)
     torch.cuda.synchronize()
     assert torch.equal(a, b) and torch.equal(g1, g2)
-    assert rel(host(x1), host(x2)) < 1e-6        # spread: atomics reorder rounding only
+    assert rel(host(x1), host(x2)) < 1e-6        # spread: heavy-tile atomics reorder rounding only
 
 
 def test_launch_counter_and_profile_hooks():
