@@ -54,7 +54,7 @@ typedef struct {
 enum {
     NUFFT_OK = 0,
     NUFFT_ERR_INVALID_ARG = -1, /* null pointer, bad size, C out of range */
-    NUFFT_ERR_UNSUPPORTED = -2, /* D not in {1,2,3}, odd N_d, J out of [2,8], grid too large */
+    NUFFT_ERR_UNSUPPORTED = -2, /* D not in {1,2,3}, odd N_d, J out of [4,8], grid too large */
     NUFFT_ERR_OOM = -3,         /* device allocation failed */
     NUFFT_ERR_CUDA = -4,        /* a CUDA runtime call or kernel launch failed */
     NUFFT_ERR_TIMEOUT = -5      /* reserved: a bounded device wait gave up */
@@ -66,7 +66,7 @@ typedef struct {
     int64_t n[3];     /* image size N_d (even), d < dim */
     double sigma;     /* oversampling factor, > 1 (0 -> 2.0); K_d = smallest even
                          2,3,5-smooth integer >= sigma N_d, K_d <= 4096 */
-    int J;            /* interpolation width, 2..8 (0 -> 6) */
+    int J;            /* interpolation width, 4..8 (0 -> 6) */
     double beta;      /* Kaiser-Bessel shape (<= 0 -> Beatty et al.:
                          pi sqrt((J/sigma)^2 (sigma-1/2)^2 - 0.8)) */
     int max_coils;    /* largest C any call on this plan will pass, 1..128 (0 -> 1) */

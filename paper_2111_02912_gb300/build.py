@@ -10,7 +10,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libnufftjac.so")
-SOURCES = ["kernels_gather_d3.cu", "kernels_gather_d2.cu", "kernels_gather_d1.cu", "nufft_api.cu", "kernels_sort.cu",
+SOURCES = ["kernels_fft2_fwd_mid.cu", "kernels_fft2_fwd_first.cu", "kernels_fft2_inv_mid.cu", "kernels_fft2_inv_last.cu",
+           "kernels_gather_d3.cu", "kernels_gather_d2.cu", "kernels_gather_d1.cu", "nufft_api.cu", "kernels_sort.cu",
            "kernels_fft.cu", "kernels_spread.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--extended-lambda",
@@ -28,7 +29,7 @@ def build(verbose=False, force=False):
     """Compile every CUDA translation unit and link the shared library; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, h) for h in ("common.cuh", "internal.h", "interp.cuh")] + \
+    deps = srcs + [os.path.join(CSRC, h) for h in ("common.cuh", "internal.h", "interp.cuh", "fft_dft.cuh", "fft_twostep.cuh")] + \
         [os.path.join(ROOT, "include", "nufftjac.h"), os.path.join(CSRC, "exports.map")]
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(p) for p in deps + [os.path.abspath(__file__)])

@@ -113,6 +113,26 @@ struct LinePass {
 enum PassKind { PASS_FWD_FIRST, PASS_FWD_MID, PASS_INV_MID, PASS_INV_LAST };
 cudaError_t launch_line_pass(PassKind kind, const LinePass& a, dim3 grid, int threads, size_t smem,
                              cudaStream_t s);
+// Register-resident two-phase passes (k_line_fft2): factorisations L = L1 L2
+// with a compiled kernel, X(L1, L2), L1 <= L2 <= 32.  Launch with TL lines per
+// block (power of two, TL L2 threads, a multiple of 32, at most 512) and
+// TL (L + 1) complex of dynamic shared memory.
+#define NJ_FFT2_SIZES(X) \
+    X(8, 8) X(8, 10) X(8, 12) X(8, 16) X(10, 16) X(12, 16) X(12, 20) X(16, 16) \
+    X(16, 20) X(16, 24) X(20, 20) X(20, 24) X(16, 32) X(20, 32) X(24, 32) X(32, 32)
+template <PassKind KIND>
+cudaError_t launch_fft2_kind(int L1, int L2, const LinePass& a, dim3 grid, int threads, size_t smem, cudaStream_t s);
+inline bool fft2_factor(int L, int& L1, int& L2) {
+#define NJ_FFT2_MATCH(A, B) \
+    if (L == (A) * (B)) {   \
+        L1 = A;             \
+        L2 = B;             \
+        return true;        \
+    }
+    NJ_FFT2_SIZES(NJ_FFT2_MATCH)
+#undef NJ_FFT2_MATCH
+    return false;
+}
 // x[i] = sum_k part[k * n + i] for k < nparts, in order (the coil-sum chunks of PASS_INV_LAST).
 cudaError_t launch_sum_chunks(const float2* part, int nparts, int64_t n, float2* x, cudaStream_t s);
 

@@ -26,121 +26,10 @@
 // pass applies the scaling, conj(s_c) and the coil sum.
 #include <algorithm>
 
+#include "fft_dft.cuh"
 #include "internal.h"
 
 namespace nj {
-
-template <int DIR>
-__device__ __forceinline__ float2 mul_si(float2 z) {   // (DIR * i) * z
-    return DIR < 0 ? make_float2(z.y, -z.x) : make_float2(-z.y, z.x);
-}
-
-// In-register R-point DFT with exp(DIR * 2 pi i n k / R).
-template <int R, int DIR>
-struct Dft;
-
-template <int DIR>
-struct Dft<2, DIR> {
-    __device__ __forceinline__ static void run(float2* a) {
-        const float2 t = a[1];
-        a[1] = csub(a[0], t);
-        a[0] = cadd(a[0], t);
-    }
-};
-
-template <int DIR>
-struct Dft<4, DIR> {
-    __device__ __forceinline__ static void run(float2* a) {
-        const float2 t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
-        const float2 t2 = cadd(a[1], a[3]), t3 = mul_si<DIR>(csub(a[1], a[3]));
-        a[0] = cadd(t0, t2);
-        a[2] = csub(t0, t2);
-        a[1] = cadd(t1, t3);
-        a[3] = csub(t1, t3);
-    }
-};
-
-template <int DIR>
-struct Dft<8, DIR> {
-    __device__ __forceinline__ static void run(float2* a) {
-        float2 e[4] = {a[0], a[2], a[4], a[6]};
-        float2 o[4] = {a[1], a[3], a[5], a[7]};
-        Dft<4, DIR>::run(e);
-        Dft<4, DIR>::run(o);
-        const float h = 0.70710678118654752f;
-        // o[k] *= exp(DIR 2 pi i k / 8)
-        o[1] = make_float2(h * (o[1].x - DIR * o[1].y), h * (o[1].y + DIR * o[1].x));
-        o[2] = mul_si<DIR>(o[2]);
-        o[3] = make_float2(h * (-o[3].x - DIR * o[3].y), h * (-o[3].y + DIR * o[3].x));
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            a[k] = cadd(e[k], o[k]);
-            a[k + 4] = csub(e[k], o[k]);
-        }
-    }
-};
-
-template <int DIR>
-struct Dft<3, DIR> {
-    __device__ __forceinline__ static void run(float2* a) {
-        const float s3 = 0.86602540378443865f;   // sin(2 pi / 3)
-        const float2 t1 = cadd(a[1], a[2]);
-        const float2 t2 = cscale(mul_si<DIR>(csub(a[1], a[2])), s3);
-        const float2 m = make_float2(a[0].x - 0.5f * t1.x, a[0].y - 0.5f * t1.y);
-        a[0] = cadd(a[0], t1);
-        a[1] = cadd(m, t2);
-        a[2] = csub(m, t2);
-    }
-};
-
-template <int DIR>
-struct Dft<5, DIR> {
-    __device__ __forceinline__ static void run(float2* a) {
-        const float c1 = 0.30901699437494742f, c2 = -0.80901699437494742f;   // cos(2pi/5), cos(4pi/5)
-        const float s1 = 0.95105651629515357f, s2 = 0.58778525229247313f;    // sin(2pi/5), sin(4pi/5)
-        const float2 b1 = cadd(a[1], a[4]), b2 = cadd(a[2], a[3]);
-        const float2 d1 = csub(a[1], a[4]), d2 = csub(a[2], a[3]);
-        const float2 m1 = make_float2(a[0].x + c1 * b1.x + c2 * b2.x, a[0].y + c1 * b1.y + c2 * b2.y);
-        const float2 m2 = make_float2(a[0].x + c2 * b1.x + c1 * b2.x, a[0].y + c2 * b1.y + c1 * b2.y);
-        const float2 n1 = mul_si<DIR>(make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y));
-        const float2 n2 = mul_si<DIR>(make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y));
-        a[0] = cadd(a[0], cadd(b1, b2));
-        a[1] = cadd(m1, n1);
-        a[4] = csub(m1, n1);
-        a[2] = cadd(m2, n2);
-        a[3] = csub(m2, n2);
-    }
-};
-
-template <int DIR>
-struct Dft<16, DIR> {
-    // 16 = 4 x 4: DFT4 over n1 for each n2, twiddle W16^(n2 k1), DFT4 over n2 for each k1.
-    __device__ __forceinline__ static void run(float2* a) {
-        const float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
-        // W16^m = (cos 2pi m/16, DIR sin 2pi m/16) for m = 0..9
-        const float wc[10] = {1.f, c1, h, s1, 0.f, -s1, -h, -c1, -1.f, -c1};
-        const float ws[10] = {0.f, s1, h, c1, 1.f, c1, h, s1, 0.f, -s1};
-        float2 b[4][4];
-#pragma unroll
-        for (int n2 = 0; n2 < 4; ++n2) {
-            float2 t[4] = {a[n2], a[4 + n2], a[8 + n2], a[12 + n2]};
-            Dft<4, DIR>::run(t);
-#pragma unroll
-            for (int k1 = 0; k1 < 4; ++k1) {
-                const int m = n2 * k1;
-                if (m == 0) b[n2][k1] = t[k1];
-                else b[n2][k1] = cmul(t[k1], make_float2(wc[m], DIR * ws[m]));
-            }
-        }
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) {
-            float2 t[4] = {b[0][k1], b[1][k1], b[2][k1], b[3][k1]};
-            Dft<4, DIR>::run(t);
-#pragma unroll
-            for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = t[k2];
-        }
-    }
-};
 
 // Global side of a fused first / last stage, for the one tile line a thread
 // works on (the block size is a multiple of the tile's line count, so butterfly

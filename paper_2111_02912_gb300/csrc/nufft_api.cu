@@ -359,16 +359,51 @@ int do_set_points(nufft_plan_s* p, int64_t m, const float* omega, cudaStream_t s
     return NUFFT_OK;
 }
 
+// Two-phase line pass of kind `kind` (kernels instantiated one kind per translation unit).
+cudaError_t launch_line_pass2(PassKind kind, int L1, int L2, const LinePass& a, dim3 grid, int threads,
+                                     size_t smem, cudaStream_t s) {
+    switch (kind) {
+        case PASS_FWD_FIRST: return launch_fft2_kind<PASS_FWD_FIRST>(L1, L2, a, grid, threads, smem, s);
+        case PASS_FWD_MID: return launch_fft2_kind<PASS_FWD_MID>(L1, L2, a, grid, threads, smem, s);
+        case PASS_INV_MID: return launch_fft2_kind<PASS_INV_MID>(L1, L2, a, grid, threads, smem, s);
+        default: return launch_fft2_kind<PASS_INV_LAST>(L1, L2, a, grid, threads, smem, s);
+    }
+}
+
 // Tile shape of a line pass: TL lines (TB rows x TS channels) of length L.
+// L1 > 0: the register-resident two-phase kernel for L = L1 L2; else the
+// shared-memory Stockham kernel.
 struct Tile {
     int TB, TS, TL, threads;
     size_t smem;
+    int L1, L2, LP;   // two-phase kernel: factors and shared line pitch
 };
+
 Tile pick_tile(int L, int64_t B, int64_t S, bool coil_sum, int n_out) {
+    Tile t{};
+    if (fft2_factor(L, t.L1, t.L2)) {
+        // 8 adjacent lines (64-byte segments along the channel axis), two blocks per SM:
+        // measured faster than 4 or 16 lines on the 640-point passes
+        int TL = 8;
+        t.TS = std::min<int>(TL, pow2_ceil(S));
+        t.TB = std::min<int>(TL / t.TS, pow2_ceil(B));
+        t.TL = t.TB * t.TS;
+        while ((t.TL * t.L2) % 32 != 0) {   // whole warps; extra lines are masked
+            t.TB *= 2;
+            t.TL *= 2;
+        }
+        t.threads = t.TL * t.L2;
+        // line pitch: >= L1 (L2 + 1), congruent to 16 / H mod 16 for H lines per half-warp
+        const int H = std::min(t.TL, 16), want = H == 16 ? 1 : 16 / H;
+        t.LP = t.L1 * (t.L2 + 1);
+        while (t.LP % 16 != want) ++t.LP;
+        t.smem = (size_t)t.TL * t.LP * sizeof(float2);
+        return t;
+    }
+    t.L1 = t.L2 = 0;
     const size_t budget = 58 * 1024;   // three to four blocks per SM
     int TL = 32;
     while (TL > 1 && (size_t)(2 * (size_t)L * (TL + 1) + L) * sizeof(float2) > budget) TL /= 2;
-    Tile t;
     t.TS = std::min<int>(TL, pow2_ceil(S));
     t.TB = std::min<int>(TL / t.TS, pow2_ceil(B));
     t.TL = t.TB * t.TS;
@@ -420,7 +455,7 @@ int forward_grids(nufft_plan_s* p, int C, int nd, int has_plain, const float2* x
         a.TS = t.TS;
         a.lgTS = ilog2(t.TS);
         a.lgTL = ilog2(t.TL);
-        a.TLP = t.TL + 1;
+        a.TLP = t.L1 ? t.LP : t.TL + 1;
         a.nchunks = 1;
         a.coil_sum = 0;
         a.in = in;
@@ -431,8 +466,10 @@ int forward_grids(nufft_plan_s* p, int C, int nd, int has_plain, const float2* x
         a.ntiles_s = (S + t.TS - 1) / t.TS;
         dim3 grid((unsigned)(((B + t.TB - 1) / t.TB) * a.ntiles_s));
         const PassKind kind = (k == 0) ? PASS_FWD_FIRST : PASS_FWD_MID;
-        int st = launch(p, k == 0 ? PK_FFT_FWD_FIRST : PK_FFT_FWD_MID, s,
-                        [&] { return launch_line_pass(kind, a, grid, t.threads, t.smem, s); });
+        int st = launch(p, k == 0 ? PK_FFT_FWD_FIRST : PK_FFT_FWD_MID, s, [&] {
+            return t.L1 ? launch_line_pass2(kind, t.L1, t.L2, a, grid, t.threads, t.smem, s)
+                        : launch_line_pass(kind, a, grid, t.threads, t.smem, s);
+        });
         if (st) return st;
         in = out;
     }
@@ -501,7 +538,7 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
         a.TS = t.TS;
         a.lgTS = ilog2(t.TS);
         a.lgTL = ilog2(t.TL);
-        a.TLP = t.TL + 1;
+        a.TLP = t.L1 ? t.LP : t.TL + 1;
         a.coil_sum = coil_sum ? 1 : 0;
         a.nchunks = 1;   // one channel chunk per block; chunks are blockIdx.y
         const int chunks = (int)((S + t.TS - 1) / t.TS);
@@ -519,8 +556,10 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
         a.ntiles_s = chunks;
         dim3 grid((unsigned)(((B + t.TB - 1) / t.TB) * chunks));
         const PassKind kind = last ? PASS_INV_LAST : PASS_INV_MID;
-        st = launch(p, last ? PK_FFT_INV_LAST : PK_FFT_INV_MID, s,
-                    [&] { return launch_line_pass(kind, a, grid, t.threads, t.smem, s); });
+        st = launch(p, last ? PK_FFT_INV_LAST : PK_FFT_INV_MID, s, [&] {
+            return t.L1 ? launch_line_pass2(kind, t.L1, t.L2, a, grid, t.threads, t.smem, s)
+                        : launch_line_pass(kind, a, grid, t.threads, t.smem, s);
+        });
         if (st) return st;
         if (part) {
             st = launch(p, PK_SUM_CHUNKS, s, [&] { return launch_sum_chunks(part, chunks, p->Nimg, xout, s); });
