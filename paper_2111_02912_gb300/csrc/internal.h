@@ -184,7 +184,7 @@ struct SpreadArgs {
 cudaError_t launch_spread(const SpreadArgs& a, int cpl, cudaStream_t s, size_t smem);
 cudaError_t launch_zero_heavy_tiles(const SpreadArgs& a, cudaStream_t s);
 int spread_min_slots(int D, int J);   // fewest tap slots per warp the spread kernel supports
-// Cell-owner spread: D in {2, 3}, every tile edge <= K - J + 1 and >= J - 1, prod B <= 512,
+// Tile spread (row owners in 2-D, cell owners in 3-D): D in {2, 3}, every tile edge <= K - J + 1 and >= J - 1, prod B <= 512,
 // a.CC = coils per block (4, 8 or 16), a.P candidates per work item (<= prod B).
 cudaError_t launch_spread_cells(const SpreadArgs& a, cudaStream_t s);
 

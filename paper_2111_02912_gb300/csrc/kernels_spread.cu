@@ -20,6 +20,8 @@
 // window start, so consecutive points that share a window (dense sampling
 // near the k-space centre) are summed in registers and added to the shared
 // tile once per run.
+#include <algorithm>
+
 #include "interp.cuh"
 
 namespace nj {
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(256, 2) k_spread(SpreadArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Cell-owner spread (fast path).  Used when no window can cover a tile twice
+// Cell-owner spread (fast path in 3-D).  Used when no window can cover a tile twice
 // (every tile edge Bt_d <= K_d - J + 1) and tiles are at least J - 1 wide.
 // The block stages the work item's candidates (one per thread), keeps those
 // whose window reaches the tile, and counting-sorts them in shared memory by
@@ -499,12 +501,263 @@ static cudaError_t spread_cells_d(const SpreadArgs& a, cudaStream_t s, int threa
     }
 }
 
-cudaError_t launch_spread_cells(const SpreadArgs& a, cudaStream_t s) {
+static cudaError_t launch_spread_cells_3d(const SpreadArgs& a, cudaStream_t s) {
     if (a.max_items == 0) return cudaSuccess;
     int threads = 1;
     for (int d = 0; d < a.D; ++d) threads *= a.B[d];
-    if (a.D == 2) return spread_cells_d<2>(a, s, threads);
     return spread_cells_d<3>(a, s, threads);
+}
+
+// ---------------------------------------------------------------------------
+// Row-owner spread (fast path in 2-D).  Used when no window can cover a tile twice
+// (every tile edge Bt_d <= K_d - J + 1) and tiles are at least J - 1 wide.
+// The block stages the work item's candidates (one per thread), keeps those
+// whose window reaches the tile and counting-sorts them in shared memory by
+// the outer coordinates of their window start, e_d = start_d - org_d + J - 1
+// in [0, Bt_d + J - 1) (bucket e_0 in 2-D, (e_0, e_1) in 3-D).
+//
+// The tile (all coils of the block's chunk) is accumulated in shared memory.
+// Its rows (all axes but the last) are cut into units of a row segment, and
+// warp w owns the units u = w mod (warps): the points covering row l are those
+// of the J (2-D) or J^2 (3-D) buckets with e_d in [l_d, l_d + J - 1], with
+// outer taps j_d = l_d + J - 1 - e_d.  For each such point the warp's lanes
+// take (last-axis tap, coil) pairs and add w * y to the cells of the row that
+// fall inside the unit: no two lanes of a warp, and no two warps, ever write
+// the same cell, so the tile needs no atomics.  Heavy tiles (several work
+// items) are cleared first and receive float2 vector atomics; the order of the
+// sums follows the (arrival-ordered) hit list, so results agree to rounding.
+template <int D, int J, int CPT>
+__global__ void __launch_bounds__(512) k_spread_rows(SpreadArgs a) {
+    extern __shared__ float4 smem4[];
+    __shared__ float coef[kKbTerms];
+    __shared__ int s_start[27], s_pref[28], s_nn, s_nh;
+    const int it = blockIdx.x;
+    if (it >= a.nitems[0]) return;     // block-uniform
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = nt >> 5;
+    const int4 item = a.items[it];
+    const int tile = item.x, part = item.y, nparts = item.z;
+    int org[kMaxDim] = {0, 0, 0}, Bt[kMaxDim] = {1, 1, 1}, Kd[kMaxDim] = {1, 1, 1}, E[kMaxDim] = {1, 1, 1};
+    {
+        int r = tile;
+        for (int d = D - 1; d >= 0; --d) {
+            const int nbd = a.nb[d];
+            const int bc = r % nbd;
+            r /= nbd;
+            Kd[d] = a.K[d];
+            org[d] = bc * a.B[d];
+            Bt[d] = min(a.B[d], Kd[d] - org[d]);
+            E[d] = Bt[d] + J - 1;
+        }
+    }
+    const int NB = D == 2 ? E[0] : E[0] * E[1];   // buckets
+    const int P = a.P;
+    const int c0 = blockIdx.y * CPT;
+    const int ncc = min(CPT, a.C - c0);
+    const int tcells = Bt[0] * Bt[1] * Bt[2];
+    const int Bl = Bt[D - 1];
+    const int R = tcells / Bl;                    // tile rows
+    // shared: tile [tcells][CPT], y [P][YP], weights [P][WP], last start e_l [P], bucket [P],
+    // sorted hits [P], bucket offsets [NB + 1], cursors [NB]; odd row pitches YP, WP keep the
+    // one-candidate-per-thread staging stores on distinct banks
+    constexpr int YP = CPT + 1, WP = D * J + ((D * J + 1) & 1);
+    float2* s_acc = (float2*)smem4;
+    float2* s_y = s_acc + (size_t)tcells * CPT;
+    float* s_w = (float*)(s_y + (size_t)P * YP);
+    int* s_el = (int*)(s_w + P * WP);
+    int* s_bk = s_el + P;
+    int* s_list = s_bk + P;
+    int* s_off = s_list + P;
+    int* s_cur = s_off + NB + 1;
+
+    if (tid < kKbTerms) coef[tid] = a.kb.a[tid];
+    {
+        const int* tn = a.tile_nbr + (int64_t)tile * kNbrStride;
+        if (tid == 0) { s_nn = tn[0]; s_nh = 0; }
+        if (tid < 27) s_start[tid] = tn[1 + 2 * tid];      // entries past the count are never used
+        if (tid < 28) s_pref[tid] = tn[2 + 2 * tid];
+    }
+    for (int i = tid; i < tcells * CPT; i += nt) s_acc[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < NB; i += nt) s_cur[i] = 0;
+    __syncthreads();
+
+    // ------------------------------------------------ stage and count the hits
+    const int nn = s_nn;
+    const int lo = part * P, hi = min(s_pref[nn], lo + P);
+    for (int t = tid; t < P; t += nt) {
+        const int cand = lo + t;
+        if (cand >= hi) break;
+        int q = 0;
+        while (q + 1 < nn && s_pref[q + 1] <= cand) ++q;
+        const int64_t pidx = s_start[q] + (cand - s_pref[q]);
+        const int4 ix = a.pts.idx[pidx];
+        bool hit = true;
+        int e[kMaxDim] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            int sd = (d == 0 ? ix.x : (d == 1 ? ix.y : ix.z)) - org[d];
+            if (sd < 0) sd += Kd[d];
+            if (sd > Kd[d] - J) sd -= Kd[d];           // starts up to J-1 cells before the tile
+            hit = hit && sd >= -(J - 1) && sd < Bt[d];
+            e[d] = sd + J - 1;
+        }
+        if (!hit) continue;
+        const int slot = atomicAdd(&s_nh, 1);
+        const int bk = D == 2 ? e[0] : e[0] * E[1] + e[1];
+        s_el[slot] = e[D - 1] - (J - 1);               // window start along the last axis, tile-relative
+        s_bk[slot] = bk;
+        const float4 fr = a.pts.frac[pidx];
+        float* w = s_w + slot * WP;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const float u0 = d == 0 ? fr.x : (d == 1 ? fr.y : fr.z);
+#pragma unroll
+            for (int j = 0; j < J; ++j) w[d * J + j] = kb_psi(coef, a.kb.two_over_j, u0 - (float)j);
+        }
+        float2* yv = s_y + (size_t)slot * YP;
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+            yv[c] = c < ncc ? __ldg(a.y + (int64_t)(c0 + c) * a.M + ix.w) : make_float2(0.f, 0.f);
+        atomicAdd(&s_cur[bk], 1);
+    }
+    __syncthreads();
+    // exclusive scan of the bucket counts (one warp)
+    if (warp == 0) {
+        int carry = 0;
+        for (int b0 = 0; b0 < NB; b0 += 32) {
+            const int b = b0 + lane;
+            const int v = b < NB ? s_cur[b] : 0;
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (b < NB) {
+                s_off[b] = carry + incl - v;
+                s_cur[b] = carry + incl - v;
+            }
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) s_off[NB] = carry;
+    }
+    __syncthreads();
+    const int nh = s_nh;
+    for (int h = tid; h < nh; h += nt) s_list[atomicAdd(&s_cur[s_bk[h]], 1)] = h;
+    __syncthreads();
+
+    // ------------------------------------------------------------- accumulate
+    constexpr int JPL = 32 / CPT;                 // last-axis taps per lane pass
+    constexpr int NJX = (J + JPL - 1) / JPL;      // passes
+    const int c = lane & (CPT - 1), jg = lane / CPT;
+    const int nseg = R >= NW ? 1 : (NW + R - 1) / R;   // row segments when rows are fewer than warps
+    const int segw = (Bl + nseg - 1) / nseg;
+    for (int u = warp; u < R * nseg; u += NW) {
+        const int r = u / nseg, sg = u - r * nseg;
+        const int x_lo = sg * segw, x_hi = min(Bl, x_lo + segw);
+        int l0 = r, l1 = 0;
+        if (D == 3) {
+            l0 = r / Bt[1];
+            l1 = r - l0 * Bt[1];
+        }
+        float2* arow = s_acc + (size_t)r * Bl * CPT + c;
+#pragma unroll 1
+        for (int a0 = 0; a0 < J; ++a0) {
+#pragma unroll 1
+            for (int a1 = 0; a1 < (D > 2 ? J : 1); ++a1) {
+                const int b = D == 2 ? l0 + a0 : (l0 + a0) * E[1] + (l1 + a1);
+                const int h1 = s_off[b + 1];
+                for (int hh = s_off[b]; hh < h1; ++hh) {
+                    const int h = s_list[hh];
+                    const float* w = s_w + h * WP;
+                    float wo = w[J - 1 - a0];
+                    if (D > 2) wo *= w[J + J - 1 - a1];
+                    const float2 yv = s_y[(size_t)h * YP + c];
+                    const int sl = s_el[h];
+#pragma unroll
+                    for (int k = 0; k < NJX; ++k) {
+                        const int jx = jg + k * JPL;
+                        const int col = sl + jx;
+                        if (jx < J && col >= x_lo && col < x_hi) {
+                            const float wt = wo * w[(D - 1) * J + jx];
+                            float2* t = arow + col * CPT;
+                            float2 v = *t;
+                            v.x = fmaf(wt, yv.x, v.x);
+                            v.y = fmaf(wt, yv.y, v.y);
+                            *t = v;
+                        }
+                    }
+                    __syncwarp();   // the next point's cells may be another lane's
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // write the tile coil-fastest: a tile row is Bt_last cells, contiguous in the grid
+    const int K1 = D > 1 ? Kd[1] : 1, K2 = D > 2 ? Kd[2] : 1;
+    const int rowlen = Bl * ncc;
+    const uint32_t mg = ncc > 1 ? (uint32_t)((((uint64_t)1 << 32) + ncc - 1) / ncc) : 0u;
+    for (int f = tid; f < R * rowlen; f += nt) {
+        const int row = f / rowlen, i = f - row * rowlen;
+        const int cr = (int)div_magic((uint32_t)i, (uint32_t)ncc, mg);
+        const int cc = i - cr * ncc;
+        int r0 = row, r1 = 0;
+        if (D == 3) { r1 = row % Bt[1]; r0 = row / Bt[1]; }
+        const int64_t gcell = D == 2 ? (int64_t)(org[0] + r0) * K1 + org[1] + cr
+                                     : ((int64_t)(org[0] + r0) * K1 + (org[1] + r1)) * K2 + org[2] + cr;
+        const float2 v = s_acc[(size_t)(row * Bl + cr) * CPT + cc];
+        float2* dst = a.grid + gcell * a.C + c0 + cc;
+        if (nparts == 1) *dst = v;
+        else if (v.x != 0.f || v.y != 0.f) atomicAdd(dst, v);
+    }
+}
+
+template <int D, int J>
+static cudaError_t spread_rows_cpt(const SpreadArgs& a, cudaStream_t s, int threads) {
+    const int cpt = a.CC <= 4 ? 4 : (a.CC <= 8 ? 8 : 16);
+    int NB = 1, tcells = 1;   // buckets, tile cells
+    for (int d = 0; d < D - 1; ++d) NB *= a.B[d] + J - 1;
+    for (int d = 0; d < D; ++d) tcells *= a.B[d];
+    const int WP = D * J + ((D * J + 1) & 1);
+    const size_t smem = (size_t)tcells * cpt * sizeof(float2) + (size_t)a.P * (cpt + 1) * sizeof(float2) +
+                        (size_t)a.P * WP * sizeof(float) + 3 * (size_t)a.P * sizeof(int) +
+                        (size_t)(2 * NB + 1) * sizeof(int);
+    dim3 grid((unsigned)a.max_items, (unsigned)((a.C + cpt - 1) / cpt));
+    if (cpt == 4) {
+        ensure_smem<k_spread_rows<D, J, 4>>(smem);
+        k_spread_rows<D, J, 4><<<grid, threads, smem, s>>>(a);
+    } else if (cpt == 8) {
+        ensure_smem<k_spread_rows<D, J, 8>>(smem);
+        k_spread_rows<D, J, 8><<<grid, threads, smem, s>>>(a);
+    } else {
+        ensure_smem<k_spread_rows<D, J, 16>>(smem);
+        k_spread_rows<D, J, 16><<<grid, threads, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t spread_rows_d(const SpreadArgs& a, cudaStream_t s, int threads) {
+    switch (a.J) {
+        case 4: return spread_rows_cpt<D, 4>(a, s, threads);
+        case 5: return spread_rows_cpt<D, 5>(a, s, threads);
+        case 6: return spread_rows_cpt<D, 6>(a, s, threads);
+        case 7: return spread_rows_cpt<D, 7>(a, s, threads);
+        default: return spread_rows_cpt<D, 8>(a, s, threads);
+    }
+}
+
+// 2-D: row-owner tiles (lanes over taps and coils, measured 1.3x faster than
+// cell owners on radial 640x640 / 16 coils, where the cell owners diverge);
+// 3-D: cell owners (8 coils and 8-cell rows leave the row owners' lanes idle,
+// while each cell sums about J^3 x density hits in registers: 1.8x faster on
+// 3-D radial 256x256x192 / 8 coils).
+cudaError_t launch_spread_cells(const SpreadArgs& a, cudaStream_t s) {
+    if (a.max_items == 0) return cudaSuccess;
+    if (a.D == 3) return launch_spread_cells_3d(a, s);
+    // one staging thread per candidate slot, whole warps, at most 512
+    int threads = std::min(512, ((a.P + 31) / 32) * 32);
+    return spread_rows_d<2>(a, s, threads);
 }
 
 // Clears the cells (all coils) of the tiles that are split over several work items.

@@ -81,7 +81,7 @@ struct nufft_plan_s {
     FftAxis axis[3]{};
     // bins
     int B[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, nbins = 1, cpb = 1, P = 1024, CCmax = 1;
-    bool cell_spread = false;   // spread by the cell-owner kernel (else the general kernel)
+    bool cell_spread = false;   // spread by the row-owner tile kernel (else the general kernel)
     int64_t nkeys = 1;
     int* d_kcount = nullptr;
     int* d_bsum = nullptr;
@@ -228,7 +228,7 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
     if (tcells * sizeof(float2) > tile_budget)
         return fail(NUFFT_ERR_UNSUPPORTED, "spread tile does not fit in shared memory; reduce bin_size");
     p.CCmax = (int)std::max<size_t>(1, std::min<size_t>(32, tile_budget / (tcells * sizeof(float2))));
-    // spread path: cell-owner tiles when no window can cover a tile twice, else the general kernel
+    // spread path: row-owner tiles when no window can cover a tile twice, else the general kernel
     p.cell_spread = p.D >= 2 && tcells <= 512;
     for (int d = 0; d < p.D; ++d) p.cell_spread = p.cell_spread && p.B[d] + p.J - 1 <= p.K[d];
     p.P = p.cell_spread ? (int)tcells : (p.D == 3 ? 1024 : 512);
