@@ -35,6 +35,9 @@ struct SortArgs {
     int* nitems;      // [1]
     int4* pidx;       // [M]
     float4* pfrac;    // [M]
+    float* pw;        // [M][ws]   kernel weights psi(u0_d - j) of the sorted points
+    int ws;
+    KbPoly kb;
 };
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
 cudaError_t launch_key_count(const SortArgs& a, cudaStream_t s);

@@ -16,27 +16,19 @@
 
 namespace nj {
 
-// Weights of one sample into w[d * J + j] (shared, per group): lane q of the
-// group evaluates psi at the offsets q, q + G, ...
+// Weights of one sample into w[d * J + j] (shared, per group), copied from the
+// sort's per-point weights: lane q of the group loads q, q + G, ...
 template <int D, int J>
-__device__ __forceinline__ void group_weights(float* w, const float* coef, float two_over_j, float4 fr, int lane_g,
-                                              int G) {
-    for (int q = lane_g; q < D * J; q += G) {
-        const int d = q / J, j = q - d * J;
-        const float u0 = d == 0 ? fr.x : (d == 1 ? fr.y : fr.z);
-        w[q] = kb_psi(coef, two_over_j, u0 - (float)j);
-    }
+__device__ __forceinline__ void group_weights(float* w, const float* pw, int lane_g, int G) {
+    for (int q = lane_g; q < D * J; q += G) w[q] = __ldg(pw + q);
 }
 
 // PAIR: lane l owns the coil pairs (2 (l + k G), 2 (l + k G) + 1), read as one 16-byte load
 // (C even); otherwise lane l owns coils l + k G.
 template <int D, int J, int ND, int CPL, int MODE, bool PAIR>
 __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
-    __shared__ float coef[kKbTerms];
     extern __shared__ float wsm[];   // [groups][D * J]
     const int tid = threadIdx.x;
-    if (tid < kKbTerms) coef[tid] = a.kb.a[tid];
-    __syncthreads();
 
     const int G = a.G;
     const int lane_g = tid & (G - 1);
@@ -48,7 +40,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
     int4 ix = make_int4(0, 0, 0, 0);
     if (valid) {
         ix = a.pts.idx[pt];
-        group_weights<D, J>(w, coef, a.kb.two_over_j, a.pts.frac[pt], lane_g, G);
+        group_weights<D, J>(w, a.pts.w + pt * a.pts.ws, lane_g, G);
     }
     __syncwarp();
     if (!valid) return;

@@ -191,6 +191,12 @@ __global__ void k_bin_scatter(SortArgs a) {
     const int dst = a.kcount[a.keyid[i]] + a.local[i];
     a.pidx[dst] = ix;
     a.pfrac[dst] = fr;
+    // the D*J kernel weights, evaluated once here and read by every gather and spread
+    float* w = a.pw + (int64_t)dst * a.ws;
+    for (int d = 0; d < a.D; ++d) {
+        const float u0 = d == 0 ? fr.x : (d == 1 ? fr.y : fr.z);
+        for (int j = 0; j < a.J; ++j) w[d * a.J + j] = kb_psi(a.kb.a, a.kb.two_over_j, u0 - (float)j);
+    }
 }
 
 __global__ void k_bin_items(SortArgs a) {

@@ -46,7 +46,6 @@ __global__ void __launch_bounds__(256, 2) k_spread(SpreadArgs a) {
     using SH = SpreadShape<D, J>;
     constexpr int JO = SH::JO, JI = SH::JI, NR = SH::NR;
     extern __shared__ float4 smem4[];
-    __shared__ float coef[kKbTerms];
     __shared__ int s_start[27], s_pref[28], s_nn;
     __shared__ float s_w[kSpreadWarps][32][D * J + 1];                 // kernel weights per staged candidate
     __shared__ int4 s_ix[kSpreadWarps][32];                            // window start, original index
@@ -74,7 +73,6 @@ __global__ void __launch_bounds__(256, 2) k_spread(SpreadArgs a) {
     const int tcells = Bt[0] * Bt[1] * Bt[2];
     float2* tl = (float2*)smem4;   // [tcells][CC]
 
-    if (tid < kKbTerms) coef[tid] = a.kb.a[tid];
     {   // bins that reach this tile (listed by the sort)
         const int* tn = a.tile_nbr + (int64_t)tile * kNbrStride;
         if (tid == 0) s_nn = tn[0];
@@ -95,7 +93,6 @@ __global__ void __launch_bounds__(256, 2) k_spread(SpreadArgs a) {
     const int slot = lane / CCW, cw = lane - slot * CCW;
     const int nn = s_nn;
     const int lo = part * a.P, hi = min(s_pref[nn], lo + a.P);
-    const float two_over_j = a.kb.two_over_j;
     int q = 0;   // neighbour-bin cursor of this lane's staged candidate
 
     for (int cp = 0; cp < ncc; cp += CCW) {
@@ -185,13 +182,9 @@ __global__ void __launch_bounds__(256, 2) k_spread(SpreadArgs a) {
                     inside = inside && lend < Bt[d];
                 }
                 if (hit) {
-                    const float4 fr = a.pts.frac[p];
+                    const float* pw = a.pts.w + (int64_t)p * a.pts.ws;
 #pragma unroll
-                    for (int d = 0; d < D; ++d) {
-                        const float u0 = d == 0 ? fr.x : (d == 1 ? fr.y : fr.z);
-#pragma unroll
-                        for (int j = 0; j < J; ++j) s_w[warp][lane][d * J + j] = kb_psi(coef, two_over_j, u0 - (float)j);
-                    }
+                    for (int q = 0; q < D * J; ++q) s_w[warp][lane][q] = __ldg(pw + q);
                     for (int cc = 0; cc < nyc; ++cc)
                         s_y[warp][lane][cc] = __ldg(a.y + (int64_t)(c0 + cp + cc) * a.M + ix.w);
                     s_ix[warp][lane] = make_int4(ix.x, ix.y, ix.z, inside ? 1 : 0);
@@ -276,7 +269,6 @@ __global__ void __launch_bounds__(256, 2) k_spread(SpreadArgs a) {
 template <int D, int J, int CPT>
 __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
     extern __shared__ float4 smem4[];
-    __shared__ float coef[kKbTerms];
     __shared__ int s_start[27], s_pref[28], s_nn, s_nh;
     const int it = blockIdx.x;
     if (it >= a.nitems[0]) return;     // block-uniform
@@ -311,7 +303,6 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
     int* s_list = s_orig + P;
     int* s_cnt = s_list + P;
 
-    if (tid < kKbTerms) coef[tid] = a.kb.a[tid];
     {
         const int* tn = a.tile_nbr + (int64_t)tile * kNbrStride;
         if (tid == 0) { s_nn = tn[0]; s_nh = 0; }
@@ -348,14 +339,10 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
             s_el[my_slot] = e[D - 1];
             s_row[my_slot] = my_row;
             s_orig[my_slot] = my_orig;
-            const float4 fr = a.pts.frac[p];
+            const float* pw = a.pts.w + p * a.pts.ws;
             float* w = s_w + my_slot * (D * J);
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const float u0 = d == 0 ? fr.x : (d == 1 ? fr.y : fr.z);
-#pragma unroll
-                for (int j = 0; j < J; ++j) w[d * J + j] = kb_psi(coef, a.kb.two_over_j, u0 - (float)j);
-            }
+            for (int q = 0; q < D * J; ++q) w[q] = __ldg(pw + q);
             float2* yv = s_y + (size_t)my_slot * (CPT + 1);
 #pragma unroll
             for (int c = 0; c < CPT; ++c)
@@ -529,7 +516,6 @@ static cudaError_t launch_spread_cells_3d(const SpreadArgs& a, cudaStream_t s) {
 template <int D, int J, int CPT>
 __global__ void __launch_bounds__(512) k_spread_rows(SpreadArgs a) {
     extern __shared__ float4 smem4[];
-    __shared__ float coef[kKbTerms];
     __shared__ int s_start[27], s_pref[28], s_nn, s_nh;
     const int it = blockIdx.x;
     if (it >= a.nitems[0]) return;     // block-uniform
@@ -569,7 +555,6 @@ __global__ void __launch_bounds__(512) k_spread_rows(SpreadArgs a) {
     int* s_off = s_list + P;
     int* s_cur = s_off + NB + 1;
 
-    if (tid < kKbTerms) coef[tid] = a.kb.a[tid];
     {
         const int* tn = a.tile_nbr + (int64_t)tile * kNbrStride;
         if (tid == 0) { s_nn = tn[0]; s_nh = 0; }
@@ -605,14 +590,10 @@ __global__ void __launch_bounds__(512) k_spread_rows(SpreadArgs a) {
         const int bk = D == 2 ? e[0] : e[0] * E[1] + e[1];
         s_el[slot] = e[D - 1] - (J - 1);               // window start along the last axis, tile-relative
         s_bk[slot] = bk;
-        const float4 fr = a.pts.frac[pidx];
+        const float* pw = a.pts.w + pidx * a.pts.ws;
         float* w = s_w + slot * WP;
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-            const float u0 = d == 0 ? fr.x : (d == 1 ? fr.y : fr.z);
-#pragma unroll
-            for (int j = 0; j < J; ++j) w[d * J + j] = kb_psi(coef, a.kb.two_over_j, u0 - (float)j);
-        }
+        for (int q = 0; q < D * J; ++q) w[q] = __ldg(pw + q);
         float2* yv = s_y + (size_t)slot * YP;
 #pragma unroll
         for (int c = 0; c < CPT; ++c)

@@ -95,6 +95,8 @@ struct nufft_plan_s {
     int* d_keyid = nullptr;
     int4* d_pidx = nullptr;
     float4* d_pfrac = nullptr;
+    float* d_pw = nullptr;   // [M_cap][ws] kernel weights of the sorted points
+    int ws = 4;              // D*J rounded up to a multiple of 4
     float c_hi[3] = {0, 0, 0}, c_lo[3] = {0, 0, 0};
     // workspace
     float2* d_G = nullptr;
@@ -177,6 +179,7 @@ void free_plan(nufft_plan_s* p) {
     for (int d = 0; d < 3; ++d) { cudaFree(p->d_deap[d]); cudaFree(p->d_tw[d]); }
     cudaFree(p->d_kcount); cudaFree(p->d_bsum); cudaFree(p->d_offsets); cudaFree(p->d_item_off); cudaFree(p->d_tile_parts); cudaFree(p->d_tile_nbr);
     cudaFree(p->d_nitems); cudaFree(p->d_items); cudaFree(p->d_local); cudaFree(p->d_keyid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
+    cudaFree(p->d_pw);
     cudaFree(p->d_G); cudaFree(p->d_T);
     for (auto& e : p->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto e : p->pool) cudaEventDestroy(e);
@@ -242,6 +245,7 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
     }
     if (ak > 1e-9 * sum) return fail(NUFFT_ERR_UNSUPPORTED, "beta too large for the kernel power series");
     p.kb.two_over_j = (float)(2.0 / p.J);
+    p.ws = (p.D * p.J + 3) & ~3;
     for (int d = 0; d < p.D; ++d) {
         const double c = (double)p.K[d] / (2.0 * M_PI);
         p.c_hi[d] = (float)c;
@@ -285,19 +289,23 @@ size_t max_items(const nufft_plan_s& p, int64_t cap) {
 }
 
 size_t point_bytes(const nufft_plan_s& p, int64_t cap) {
-    size_t b = (size_t)cap * (2 * sizeof(int) + sizeof(int4) + sizeof(float4)) + max_items(p, cap) * sizeof(int4);
+    size_t b = (size_t)cap * (2 * sizeof(int) + sizeof(int4) + sizeof(float4) + p.ws * sizeof(float)) +
+               max_items(p, cap) * sizeof(int4);
     return b;
 }
 
 int alloc_points(nufft_plan_s* p, int64_t cap) {
     cudaFree(p->d_items); cudaFree(p->d_local); cudaFree(p->d_keyid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
+    cudaFree(p->d_pw);
     p->d_items = nullptr; p->d_local = p->d_keyid = nullptr; p->d_pidx = nullptr; p->d_pfrac = nullptr;
+    p->d_pw = nullptr;
     const size_t c = (size_t)std::max<int64_t>(cap, 1);
     if (cudaMalloc(&p->d_items, max_items(*p, cap) * sizeof(int4)) != cudaSuccess ||
         cudaMalloc(&p->d_local, c * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&p->d_keyid, c * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&p->d_pidx, c * sizeof(int4)) != cudaSuccess ||
-        cudaMalloc(&p->d_pfrac, c * sizeof(float4)) != cudaSuccess) {
+        cudaMalloc(&p->d_pfrac, c * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&p->d_pw, c * p->ws * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         return fail(NUFFT_ERR_OOM, "device allocation of point arrays failed");
     }
@@ -334,6 +342,9 @@ SortArgs sort_args(nufft_plan_s* p, const float* omega) {
     a.nitems = p->d_nitems;
     a.pidx = p->d_pidx;
     a.pfrac = p->d_pfrac;
+    a.pw = p->d_pw;
+    a.ws = p->ws;
+    a.kb = p->kb;
     return a;
 }
 
@@ -482,7 +493,7 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
     int st;
     // spread: output-driven tiles; only tiles split over several work items are cleared first
     SpreadArgs sa{};
-    sa.pts = PointsView{p->d_pidx, p->d_pfrac, p->M};
+    sa.pts = PointsView{p->d_pidx, p->d_pfrac, p->M, p->d_pw, p->ws};
     sa.D = D;
     sa.J = p->J;
     for (int d = 0; d < 3; ++d) {
@@ -572,7 +583,7 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
 
 GatherArgs gather_args(nufft_plan_s* p, int C, int nd, int has_plain) {
     GatherArgs g{};
-    g.pts = PointsView{p->d_pidx, p->d_pfrac, p->M};
+    g.pts = PointsView{p->d_pidx, p->d_pfrac, p->M, p->d_pw, p->ws};
     g.D = p->D;
     g.J = p->J;
     for (int d = 0; d < 3; ++d) g.K[d] = (int)p->K[d];
@@ -902,6 +913,7 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
                  o_tile_nbr = cv.take<int>((size_t)kNbrStride * p.nbins),
                  o_nitems = cv.take<int>(1), o_items = cv.take<int4>(max_items(p, mc)), o_local = cv.take<int>(mc),
                  o_keyid = cv.take<int>(mc), o_pidx = cv.take<int4>(mc), o_pfrac = cv.take<float4>(mc),
+                 o_pw = cv.take<float>((size_t)mc * p.ws),
                  o_G = cv.take<float2>(G), o_T = cv.take<float2>(T);
     if (cv.off > (size_t)NUFFT_NOALLOC_SCRATCH_BYTES)
         return fail(NUFFT_ERR_UNSUPPORTED, "problem needs " + std::to_string(cv.off) +
@@ -941,6 +953,7 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
     p.d_keyid = (int*)(b + o_keyid);
     p.d_pidx = (int4*)(b + o_pidx);
     p.d_pfrac = (float4*)(b + o_pfrac);
+    p.d_pw = (float*)(b + o_pw);
     p.d_G = (float2*)(b + o_G);
     p.d_T = (float2*)(b + o_T);
     p.G_elems = G;
