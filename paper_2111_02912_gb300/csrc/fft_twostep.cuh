@@ -99,31 +99,41 @@ __global__ void __launch_bounds__(512, 1) k_line_fft2(LinePass a) {
             }
             float2* dst = buf + ln * LP;
             for (int p = h + lane; p < L - h; p += 32) dst[p + p / L2] = make_float2(0.f, 0.f);   // zero padding
-            // image element e sits at position (e - n_in/2) mod L; a row of up to 384
-            // elements is loaded in one batch (12 per lane)
+            // image element e sits at position (e - n_in/2) mod L.  A row of up to 384
+            // elements is loaded in one batch of 12 per lane; indices are clamped so the
+            // loads are unconditional and independent (all in flight before the first use).
             const int n = a.n_in;
+            if (!ok) {
+                for (int e = lane; e < n; e += 32) {
+                    const int p = e < h ? e - h + L : e - h;
+                    dst[p + p / L2] = make_float2(0.f, 0.f);
+                }
+                continue;
+            }
+            const float wgt = kind == Dm1 ? 0.f : (kind >= 0 ? wr : 1.f);   // row factor; last-axis weight below
             for (int e0 = 0; e0 < n; e0 += 32 * 12) {
-                float2 xv[12];
-                float sc[12];
+                float2 xv[12], mv[12];
+                float dv[12];
 #pragma unroll
                 for (int q = 0; q < 12; ++q) {
-                    const int e = e0 + q * 32 + lane;
-                    xv[q] = make_float2(0.f, 0.f);
-                    sc[q] = 0.f;
-                    if (ok && e < n) {
-                        xv[q] = __ldg(xrow + e);
-                        if (mrow) xv[q] = cmul(xv[q], __ldg(mrow + e));
-                        sc[q] = rs * __ldg(deap_last + e);
-                        if (kind == Dm1) sc[q] *= (float)(e - nlast / 2);
-                        else if (kind >= 0) sc[q] *= wr;
-                    }
+                    const int e = min(e0 + q * 32 + lane, n - 1);
+                    xv[q] = __ldg(xrow + e);
+                    dv[q] = __ldg(deap_last + e);
+                }
+                if (mrow) {
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) mv[q] = __ldg(mrow + min(e0 + q * 32 + lane, n - 1));
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) xv[q] = cmul(xv[q], mv[q]);
                 }
 #pragma unroll
                 for (int q = 0; q < 12; ++q) {
                     const int e = e0 + q * 32 + lane;
                     if (e < n) {
+                        float sc = rs * dv[q];
+                        sc *= kind == Dm1 ? (float)(e - nlast / 2) : wgt;
                         const int p = e < h ? e - h + L : e - h;
-                        dst[p + p / L2] = cscale(xv[q], sc[q]);
+                        dst[p + p / L2] = cscale(xv[q], sc);
                     }
                 }
             }

@@ -8,10 +8,8 @@
 namespace nj {
 
 // ---------------------------------------------------------------- sorting
-// Points are ordered by key = bin * cpb + cell, where the bin (a tile of B_d
-// cells per axis) and the cell inside it are those of the window start, so
-// each bin is a contiguous range sorted by cell.  cpb = prod B_d.
-constexpr int kScanPerBlock = 4096;   // keys scanned by one block of the key scan
+// Points are ordered by the bin (a tile of B_d cells per axis) of their window
+// start; each bin is a contiguous range.
 constexpr int kNbrStride = 64;        // ints per tile in tile_nbr: n, then 27 (start, prefix) pairs, total
 
 struct SortArgs {
@@ -20,12 +18,10 @@ struct SortArgs {
     int D, J;
     int K[kMaxDim];
     int B[kMaxDim], nb[kMaxDim];
-    int nbins, cpb, P;    // P: spread candidates per work item
-    int64_t nkeys;        // nbins * cpb
+    int nbins, P;         // P: spread candidates per work item
     float c_hi[kMaxDim], c_lo[kMaxDim];  // K/(2 pi) as a float pair
-    int* kcount;      // [nkeys]      points per key, then (in place) first sorted position of each key
-    int* bsum;        // [nkeys / kScanPerBlock + 1]
-    int* local;       // [M]          rank among the points of the same key
+    int* kcount;      // [nbins]      points per bin; zero before the sort, cleared again by the bin scan
+    int* local;       // [M]          rank among the points of the same bin
     int* keyid;       // [M]
     int* offsets;     // [nbins + 1]  first sorted point of each bin
     int* item_off;    // [nbins + 1]  first spread work item of each tile
@@ -40,11 +36,13 @@ struct SortArgs {
     KbPoly kb;
 };
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
-cudaError_t launch_key_count(const SortArgs& a, cudaStream_t s);
-cudaError_t launch_key_scan(const SortArgs& a, cudaStream_t s);       // three kernels
-cudaError_t launch_tile_scan(const SortArgs& a, cudaStream_t s);
-cudaError_t launch_bin_scatter(const SortArgs& a, cudaStream_t s);
-cudaError_t launch_bin_items(const SortArgs& a, cudaStream_t s);
+cudaError_t launch_key_count(const SortArgs& a, cudaStream_t s);     // histogram of bins, rank within bin
+cudaError_t launch_bin_scan(const SortArgs& a, cudaStream_t s);      // offsets; clears the histogram
+cudaError_t launch_tile_lists(const SortArgs& a, cudaStream_t s);    // reaching bins, parts per tile
+cudaError_t launch_item_scan(const SortArgs& a, cudaStream_t s);     // item offsets and list
+constexpr int kFusedTablesMaxBins = 8192;
+cudaError_t launch_sort_tables(const SortArgs& a, cudaStream_t s);   // the three above in one block
+cudaError_t launch_bin_scatter(const SortArgs& a, cudaStream_t s);   // records and weights in bin order
 
 // Bins whose points can reach tile `bin` (tiles are the bins).  A window
 // covers J cells to the right of its start, so along each axis these are the

@@ -8,12 +8,14 @@
 // integer window start and the fractional offset keep ~2^-40 relative accuracy
 // of the FP64 value although all arithmetic is FP32.
 //
-// Counting sort by key = (bin, cell of the window start): bins are tiles of
-// B_d cells per axis; inside a bin, points are ordered by the cell their
-// window starts in, so points that share a window are adjacent.  The spread
-// (the adjoint interpolation) is output-driven: tile t owns its cells and
-// takes contributions from the points of the bins that can reach it, so the
-// sort also lists the spread's work items (candidate ranges of <= P points).
+// Counting sort by the bin of the window start (bins are tiles of B_d cells
+// per axis): a histogram with atomics, one block's exclusive scan (which also
+// clears the histogram for the next sort), and a scatter that writes the
+// point records and their D*J kernel weights in bin order.  The spread (the
+// adjoint interpolation) is output-driven: tile t owns its cells and takes
+// contributions from the points of the bins that can reach it, so the sort
+// also lists, per tile, those bins and the spread's work items (candidate
+// ranges of <= P points).
 #include <algorithm>
 
 #include "internal.h"
@@ -41,13 +43,12 @@ __device__ __forceinline__ void window_of(float w, float c_hi, float c_lo, int K
 __device__ __forceinline__ void point_record(const SortArgs& a, int64_t i, int4& ix, float4& fr, int64_t& key) {
     int k0[3] = {0, 0, 0};
     float u0[3] = {0.f, 0.f, 0.f};
-    int64_t bin = 0, cell = 0;
+    int64_t bin = 0;
     for (int d = 0; d < a.D; ++d) {
         window_of(a.omega[(int64_t)d * a.m + i], a.c_hi[d], a.c_lo[d], a.K[d], a.J, k0[d], u0[d]);
         bin = bin * a.nb[d] + k0[d] / a.B[d];
-        cell = cell * a.B[d] + k0[d] % a.B[d];
     }
-    key = bin * a.cpb + cell;
+    key = bin;
     ix = make_int4(k0[0], k0[1], k0[2], (int)i);
     fr = make_float4(u0[0], u0[1], u0[2], 0.f);
 }
@@ -59,15 +60,31 @@ __global__ void k_zero(float4* p, int64_t n4, int* tail, int64_t ntail) {
     if (blockIdx.x == 0 && threadIdx.x < ntail) tail[threadIdx.x] = 0;
 }
 
+// Histogram of bins and each point's rank within its bin.  Consecutive samples
+// (a trajectory's readout) usually share a bin, so the lanes of a warp with the
+// same bin take one atomic between them: the group leader adds the group size
+// and the others offset from the returned base by their rank in the group.
 __global__ void k_key_count(SortArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.m) return;
-    int4 ix;
-    float4 fr;
-    int64_t key;
-    point_record(a, i, ix, fr, key);
-    a.keyid[i] = (int)key;
-    a.local[i] = atomicAdd(&a.kcount[key], 1);
+    const bool live = i < a.m;
+    int key = -1;
+    if (live) {
+        int4 ix;
+        float4 fr;
+        int64_t k64;
+        point_record(a, i, ix, fr, k64);
+        key = (int)k64;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (!live) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&a.kcount[key], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    a.keyid[i] = key;
+    a.local[i] = base + rank;
 }
 
 // Block-wide exclusive scan of one value per thread; returns the block total.
@@ -97,61 +114,93 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& excl) {
     return total;
 }
 
-// Pass 1: each block scans kScanPerBlock keys in place (exclusive, block-local).
-__global__ void __launch_bounds__(1024) k_scan_local(SortArgs a) {
+// One block: exclusive scan of the bin counts into offsets (offsets[nbins] = m).
+// Each thread scans a contiguous chunk; the counts are cleared on the way, so
+// the next sort needs no clearing pass.
+__global__ void __launch_bounds__(1024) k_bin_scan(SortArgs a) {
     __shared__ int sh[32];
-    constexpr int per = kScanPerBlock / 1024;
-    const int64_t base = (int64_t)blockIdx.x * kScanPerBlock + (int64_t)threadIdx.x * per;
-    int v[per], s = 0;
-#pragma unroll
-    for (int q = 0; q < per; ++q) {
-        v[q] = base + q < a.nkeys ? a.kcount[base + q] : 0;
-        s += v[q];
-    }
-    int excl;
-    const int total = block_exclusive_scan(s, sh, excl);
-#pragma unroll
-    for (int q = 0; q < per; ++q) {
-        if (base + q < a.nkeys) a.kcount[base + q] = excl;
-        excl += v[q];
-    }
-    if (threadIdx.x == 0) a.bsum[blockIdx.x] = total;
-}
-
-// Pass 2 (one block): exclusive scan of the block totals.
-__global__ void __launch_bounds__(1024) k_scan_bsum(SortArgs a, int nblk) {
-    __shared__ int sh[32];
-    const int per = (nblk + 1023) / 1024;
-    const int lo = min(nblk, (int)threadIdx.x * per), hi = min(nblk, lo + per);
+    const int n = a.nbins;
+    const int per = (n + 1023) / 1024;
+    const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
     int s = 0;
-    for (int b = lo; b < hi; ++b) s += a.bsum[b];
+    for (int b = lo; b < hi; ++b) s += a.kcount[b];
     int excl;
     block_exclusive_scan(s, sh, excl);
     for (int b = lo; b < hi; ++b) {
-        const int v = a.bsum[b];
-        a.bsum[b] = excl;
+        const int v = a.kcount[b];
+        a.offsets[b] = excl;
+        a.kcount[b] = 0;
         excl += v;
+    }
+    if (threadIdx.x == 0) a.offsets[n] = (int)a.m;
+}
+
+// Per tile: the bins that can reach it (its own and those holding the J-1
+// cells before it, at most 3^D), their point ranges as one candidate list, and
+// the number of spread work items (candidates / P, at least one).
+__global__ void k_tile_lists(SortArgs a) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= a.nbins) return;
+    int nbr[27];
+    const int nn = neighbour_bins(a.D, a.nb, a.B, a.K, a.J, b, nbr);
+    int* tn = a.tile_nbr + (int64_t)b * kNbrStride;
+    tn[0] = nn;
+    int cand = 0;
+    for (int q = 0; q < nn; ++q) {
+        const int st = a.offsets[nbr[q]];
+        tn[1 + 2 * q] = st;
+        tn[2 + 2 * q] = cand;
+        cand += a.offsets[nbr[q] + 1] - st;
+    }
+    tn[1 + 2 * nn] = 0;
+    tn[2 + 2 * nn] = cand;
+    a.tile_parts[b] = max(1, (cand + a.P - 1) / a.P);
+}
+
+// One block: exclusive scan of the work items per tile, and the item list
+// {tile, part, parts, 0}.
+__global__ void __launch_bounds__(1024) k_item_scan(SortArgs a) {
+    __shared__ int sh[32];
+    const int n = a.nbins;
+    const int per = (n + 1023) / 1024;
+    const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+    int s = 0;
+    for (int b = lo; b < hi; ++b) s += a.tile_parts[b];
+    int excl;
+    const int total = block_exclusive_scan(s, sh, excl);
+    for (int b = lo; b < hi; ++b) {
+        const int parts = a.tile_parts[b];
+        a.item_off[b] = excl;
+        for (int k = 0; k < parts; ++k) a.items[excl + k] = make_int4(b, k, parts, 0);
+        excl += parts;
+    }
+    if (threadIdx.x == 0) {
+        a.item_off[n] = total;
+        a.nitems[0] = total;
     }
 }
 
-// Pass 3: add the block offsets; record the first position of every bin.
-__global__ void k_scan_add(SortArgs a) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= a.nkeys) return;
-    const int v = a.kcount[k] + a.bsum[k / kScanPerBlock];
-    a.kcount[k] = v;
-    if (k % a.cpb == 0) a.offsets[k / a.cpb] = v;
-    if (k == a.nkeys - 1) a.offsets[a.nbins] = (int)a.m;
-}
-
-// One block: spread work items per tile (candidates = points of the bins that
-// can reach the tile, at most 3^D bins), and their exclusive scan.
-__global__ void __launch_bounds__(1024) k_tile_scan(SortArgs a) {
+// All three tables in one block when the bins are few (one launch instead of
+// three): bin offsets, the tiles' reaching bins and parts, item offsets and list.
+__global__ void __launch_bounds__(1024) k_sort_tables(SortArgs a) {
     __shared__ int sh[32];
-    const int per = (a.nbins + 1023) / 1024;
-    const int lo = min(a.nbins, (int)threadIdx.x * per), hi = min(a.nbins, lo + per);
+    const int n = a.nbins, t = threadIdx.x;
+    const int per = (n + 1023) / 1024;
+    const int lo = min(n, t * per), hi = min(n, lo + per);
+    int s = 0;
+    for (int b = lo; b < hi; ++b) s += a.kcount[b];
+    int excl;
+    block_exclusive_scan(s, sh, excl);
+    for (int b = lo; b < hi; ++b) {
+        const int v = a.kcount[b];
+        a.offsets[b] = excl;
+        a.kcount[b] = 0;
+        excl += v;
+    }
+    if (t == 0) a.offsets[n] = (int)a.m;
+    __syncthreads();   // offsets are read by other threads below (global, same block)
+    int parts_sum = 0;
     int nbr[27];
-    int si = 0;
     for (int b = lo; b < hi; ++b) {
         const int nn = neighbour_bins(a.D, a.nb, a.B, a.K, a.J, b, nbr);
         int* tn = a.tile_nbr + (int64_t)b * kNbrStride;
@@ -167,16 +216,17 @@ __global__ void __launch_bounds__(1024) k_tile_scan(SortArgs a) {
         tn[2 + 2 * nn] = cand;
         const int parts = max(1, (cand + a.P - 1) / a.P);
         a.tile_parts[b] = parts;
-        si += parts;
+        parts_sum += parts;
     }
-    int excl;
-    const int total = block_exclusive_scan(si, sh, excl);
+    const int total = block_exclusive_scan(parts_sum, sh, excl);
     for (int b = lo; b < hi; ++b) {
+        const int parts = a.tile_parts[b];
         a.item_off[b] = excl;
-        excl += a.tile_parts[b];
+        for (int k = 0; k < parts; ++k) a.items[excl + k] = make_int4(b, k, parts, 0);
+        excl += parts;
     }
-    if (threadIdx.x == 0) {
-        a.item_off[a.nbins] = total;
+    if (t == 0) {
+        a.item_off[n] = total;
         a.nitems[0] = total;
     }
 }
@@ -188,7 +238,7 @@ __global__ void k_bin_scatter(SortArgs a) {
     float4 fr;
     int64_t key;
     point_record(a, i, ix, fr, key);
-    const int dst = a.kcount[a.keyid[i]] + a.local[i];
+    const int dst = a.offsets[a.keyid[i]] + a.local[i];
     a.pidx[dst] = ix;
     a.pfrac[dst] = fr;
     // the D*J kernel weights, evaluated once here and read by every gather and spread
@@ -197,13 +247,6 @@ __global__ void k_bin_scatter(SortArgs a) {
         const float u0 = d == 0 ? fr.x : (d == 1 ? fr.y : fr.z);
         for (int j = 0; j < a.J; ++j) w[d * a.J + j] = kb_psi(a.kb.a, a.kb.two_over_j, u0 - (float)j);
     }
-}
-
-__global__ void k_bin_items(SortArgs a) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= a.nbins) return;
-    const int parts = a.tile_parts[b], base = a.item_off[b];
-    for (int k = 0; k < parts; ++k) a.items[base + k] = make_int4(b, k, parts, 0);
 }
 
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s) {
@@ -219,24 +262,25 @@ cudaError_t launch_key_count(const SortArgs& a, cudaStream_t s) {
     k_key_count<<<(unsigned)((a.m + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_key_scan(const SortArgs& a, cudaStream_t s) {
-    const int nblk = (int)((a.nkeys + kScanPerBlock - 1) / kScanPerBlock);
-    k_scan_local<<<nblk, 1024, 0, s>>>(a);
-    k_scan_bsum<<<1, 1024, 0, s>>>(a, nblk);
-    k_scan_add<<<(unsigned)((a.nkeys + 255) / 256), 256, 0, s>>>(a);
+cudaError_t launch_bin_scan(const SortArgs& a, cudaStream_t s) {
+    k_bin_scan<<<1, 1024, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_tile_scan(const SortArgs& a, cudaStream_t s) {
-    k_tile_scan<<<1, 1024, 0, s>>>(a);
+cudaError_t launch_sort_tables(const SortArgs& a, cudaStream_t s) {
+    k_sort_tables<<<1, 1024, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_tile_lists(const SortArgs& a, cudaStream_t s) {
+    k_tile_lists<<<(a.nbins + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_item_scan(const SortArgs& a, cudaStream_t s) {
+    k_item_scan<<<1, 1024, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_bin_scatter(const SortArgs& a, cudaStream_t s) {
     if (a.m == 0) return cudaSuccess;
     k_bin_scatter<<<(unsigned)((a.m + 255) / 256), 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-cudaError_t launch_bin_items(const SortArgs& a, cudaStream_t s) {
-    k_bin_items<<<(a.nbins + 255) / 256, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -16,10 +16,9 @@
 // weights and the y values go to shared memory).  It then walks the staged
 // candidates in order with its 32 lanes split into NS row slots x (32 / NS)
 // coils: lane (s, c) owns the window rows s, s + NS, ... for coil c, so no
-// two lanes of a warp ever address the same tile cell.  Points are sorted by
-// window start, so consecutive points that share a window (dense sampling
-// near the k-space centre) are summed in registers and added to the shared
-// tile once per run.
+// two lanes of a warp ever address the same tile cell.  Consecutive points
+// that share a window (dense sampling near the k-space centre) are summed in
+// registers and added to the shared tile once per run.
 #include <algorithm>
 
 #include "interp.cuh"

@@ -82,9 +82,8 @@ struct nufft_plan_s {
     // bins
     int B[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, nbins = 1, cpb = 1, P = 1024, CCmax = 1;
     bool cell_spread = false;   // spread by the row-owner tile kernel (else the general kernel)
-    int64_t nkeys = 1;
     int* d_kcount = nullptr;
-    int* d_bsum = nullptr;
+    bool kcount_clear = false;   // the bin histogram is known to be zero (the bin scan clears it)
     int* d_offsets = nullptr;
     int* d_item_off = nullptr;
     int* d_tile_parts = nullptr;
@@ -177,7 +176,7 @@ double kb_ft(double f, int J, double beta) {
 
 void free_plan(nufft_plan_s* p) {
     for (int d = 0; d < 3; ++d) { cudaFree(p->d_deap[d]); cudaFree(p->d_tw[d]); }
-    cudaFree(p->d_kcount); cudaFree(p->d_bsum); cudaFree(p->d_offsets); cudaFree(p->d_item_off); cudaFree(p->d_tile_parts); cudaFree(p->d_tile_nbr);
+    cudaFree(p->d_kcount); cudaFree(p->d_offsets); cudaFree(p->d_item_off); cudaFree(p->d_tile_parts); cudaFree(p->d_tile_nbr);
     cudaFree(p->d_nitems); cudaFree(p->d_items); cudaFree(p->d_local); cudaFree(p->d_keyid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
     cudaFree(p->d_pw);
     cudaFree(p->d_G); cudaFree(p->d_T);
@@ -225,8 +224,7 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
     for (int d = 0; d < p.D; ++d) p.nbins *= p.nb[d];
     if (p.nbins > (1 << 24)) return fail(NUFFT_ERR_UNSUPPORTED, "too many bins; enlarge bin_size");
     p.cpb = (int)tcells;
-    p.nkeys = (int64_t)p.nbins * p.cpb;
-    if (p.nkeys >= ((int64_t)1 << 31)) return fail(NUFFT_ERR_UNSUPPORTED, "grid too large for the point sort");
+    if ((int64_t)p.nbins * p.cpb >= ((int64_t)1 << 31)) return fail(NUFFT_ERR_UNSUPPORTED, "grid too large for the point sort");
     const size_t tile_budget = 32 * 1024;
     if (tcells * sizeof(float2) > tile_budget)
         return fail(NUFFT_ERR_UNSUPPORTED, "spread tile does not fit in shared memory; reduce bin_size");
@@ -327,11 +325,8 @@ SortArgs sort_args(nufft_plan_s* p, const float* omega) {
         a.c_lo[d] = p->c_lo[d];
     }
     a.nbins = p->nbins;
-    a.cpb = p->cpb;
-    a.nkeys = p->nkeys;
     a.P = p->P;
     a.kcount = p->d_kcount;
-    a.bsum = p->d_bsum;
     a.local = p->d_local;
     a.keyid = p->d_keyid;
     a.offsets = p->d_offsets;
@@ -361,12 +356,22 @@ int do_set_points(nufft_plan_s* p, int64_t m, const float* omega, cudaStream_t s
     p->last_stream = s;
     SortArgs a = sort_args(p, omega);
     int st;
-    if ((st = launch(p, PK_ZERO, s, [&] { return launch_zero(p->d_kcount, sizeof(int) * p->nkeys, s); }))) return st;
+    // the histogram is cleared only when fresh: every bin scan leaves it zero for the next sort
+    if (!p->kcount_clear &&
+        (st = launch(p, PK_ZERO, s, [&] { return launch_zero(p->d_kcount, sizeof(int) * p->nbins, s); })))
+        return st;
+    p->kcount_clear = false;
     if ((st = launch(p, PK_BIN_COUNT, s, [&] { return launch_key_count(a, s); }))) return st;
-    if ((st = launch(p, PK_BIN_SCAN, s, [&] { return launch_key_scan(a, s); }))) return st;
-    if ((st = launch(p, PK_TILE_SCAN, s, [&] { return launch_tile_scan(a, s); }))) return st;
+    if (p->nbins <= kFusedTablesMaxBins) {
+        if ((st = launch(p, PK_BIN_SCAN, s, [&] { return launch_sort_tables(a, s); }))) return st;
+        p->kcount_clear = true;
+    } else {
+        if ((st = launch(p, PK_BIN_SCAN, s, [&] { return launch_bin_scan(a, s); }))) return st;
+        p->kcount_clear = true;
+        if ((st = launch(p, PK_TILE_SCAN, s, [&] { return launch_tile_lists(a, s); }))) return st;
+        if ((st = launch(p, PK_BIN_ITEMS, s, [&] { return launch_item_scan(a, s); }))) return st;
+    }
     if ((st = launch(p, PK_BIN_SCATTER, s, [&] { return launch_bin_scatter(a, s); }))) return st;
-    if ((st = launch(p, PK_BIN_ITEMS, s, [&] { return launch_bin_items(a, s); }))) return st;
     return NUFFT_OK;
 }
 
@@ -632,7 +637,7 @@ size_t nufft_workspace_bytes(const nufft_opts* o, int64_t m) {
     size_t G, T;
     workspace_elems(p, G, T);
     size_t b = (G + T) * sizeof(float2) + point_bytes(p, std::max<int64_t>(m, 1));
-    b += (size_t)((3 + kNbrStride) * p.nbins + p.nkeys + p.nkeys / kScanPerBlock + 6) * sizeof(int);
+    b += (size_t)((4 + kNbrStride) * p.nbins + 6) * sizeof(int);
     for (int d = 0; d < p.D; ++d) b += (size_t)p.N[d] * sizeof(float) + (size_t)p.K[d] * sizeof(float2);
     return b;
 }
@@ -667,8 +672,7 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
         build_fft_axis(L, p->axis[d]);
         p->axis[d].tw = p->d_tw[d];
     }
-    if (cudaMalloc(&p->d_kcount, sizeof(int) * p->nkeys) != cudaSuccess ||
-        cudaMalloc(&p->d_bsum, sizeof(int) * (p->nkeys / kScanPerBlock + 1)) != cudaSuccess ||
+    if (cudaMalloc(&p->d_kcount, sizeof(int) * p->nbins) != cudaSuccess ||
         cudaMalloc(&p->d_offsets, sizeof(int) * (p->nbins + 1)) != cudaSuccess ||
         cudaMalloc(&p->d_item_off, sizeof(int) * (p->nbins + 1)) != cudaSuccess ||
         cudaMalloc(&p->d_tile_parts, sizeof(int) * p->nbins) != cudaSuccess ||
@@ -907,7 +911,7 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
         o_deap[d] = cv.take<float>(p.N[d]);
         o_tw[d] = cv.take<float2>(p.K[d]);
     }
-    const size_t o_kcount = cv.take<int>(p.nkeys), o_bsum = cv.take<int>(p.nkeys / kScanPerBlock + 1),
+    const size_t o_kcount = cv.take<int>(p.nbins),
                  o_offsets = cv.take<int>(p.nbins + 1),
                  o_item_off = cv.take<int>(p.nbins + 1), o_tile_parts = cv.take<int>(p.nbins),
                  o_tile_nbr = cv.take<int>((size_t)kNbrStride * p.nbins),
@@ -942,7 +946,6 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
         p.axis[d].tw = p.d_tw[d];
     }
     p.d_kcount = (int*)(b + o_kcount);
-    p.d_bsum = (int*)(b + o_bsum);
     p.d_offsets = (int*)(b + o_offsets);
     p.d_item_off = (int*)(b + o_item_off);
     p.d_tile_parts = (int*)(b + o_tile_parts);
