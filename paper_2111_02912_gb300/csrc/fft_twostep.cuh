@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(512, 1) k_line_fft2(LinePass a) {
                 sfor<0, L1>([&](auto n1_) {
                     constexpr int n1 = decltype(n1_)::value;
                     const int p = n1 * L2 + n2;
-                    v[n1] = valid ? __ldg(in_line + p * S) : make_float2(0.f, 0.f);
+                    const float2 t = __ldg(in_line + (valid ? p : 0) * S);   // unconditional load
+                    v[n1] = valid ? t : make_float2(0.f, 0.f);
                 });
             }
         }

@@ -49,8 +49,12 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
     const int chs = ND * C;   // channel stride of one grid cell
     constexpr int W = PAIR ? 2 : 1;   // coils per lane slot
     bool ok[CPL];
+    int lofs[CPL];   // coil offset of slot k; slots past the last coil read coil 0 (never stored)
 #pragma unroll
-    for (int k = 0; k < CPL; ++k) ok[k] = W * (lane_g + k * G) < C;
+    for (int k = 0; k < CPL; ++k) {
+        ok[k] = W * (lane_g + k * G) < C;
+        lofs[k] = ok[k] ? W * (lane_g + k * G) : 0;
+    }
     float2 acc[ND][CPL][W];
 #pragma unroll
     for (int q = 0; q < ND; ++q)
@@ -71,7 +75,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
         coff[j] = k * chs;
         wl[j] = w[(D - 1) * J + j];
     }
-    const float2* g0 = a.grid + W * lane_g;
+    const float2* g0 = a.grid;
 
     auto row = [&](const float2* rp, float wr) {
 #pragma unroll
@@ -81,16 +85,15 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
 #pragma unroll
             for (int q = 0; q < ND; ++q)
 #pragma unroll
-                for (int k = 0; k < CPL; ++k)
-                    if (ok[k]) {
+                for (int k = 0; k < CPL; ++k) {   // unconditional loads: all taps in flight together
                         if (PAIR) {
-                            const float4 g = __ldg((const float4*)(gp + q * C + 2 * k * G));
+                            const float4 g = __ldg((const float4*)(gp + q * C + lofs[k]));
                             acc[q][k][0].x = fmaf(wt, g.x, acc[q][k][0].x);
                             acc[q][k][0].y = fmaf(wt, g.y, acc[q][k][0].y);
                             acc[q][k][W - 1].x = fmaf(wt, g.z, acc[q][k][W - 1].x);
                             acc[q][k][W - 1].y = fmaf(wt, g.w, acc[q][k][W - 1].y);
                         } else {
-                            const float2 g = __ldg(gp + q * C + k * G);
+                            const float2 g = __ldg(gp + q * C + lofs[k]);
                             acc[q][k][0].x = fmaf(wt, g.x, acc[q][k][0].x);
                             acc[q][k][0].y = fmaf(wt, g.y, acc[q][k][0].y);
                         }

@@ -343,9 +343,11 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
 #pragma unroll
             for (int q = 0; q < D * J; ++q) w[q] = __ldg(pw + q);
             float2* yv = s_y + (size_t)my_slot * (CPT + 1);
+            float2 yl[CPT];   // all coil loads in flight at once (clamped coil, zero past the chunk)
 #pragma unroll
-            for (int c = 0; c < CPT; ++c)
-                yv[c] = c < ncc ? __ldg(a.y + (int64_t)(c0 + c) * a.M + ix.w) : make_float2(0.f, 0.f);
+            for (int c = 0; c < CPT; ++c) yl[c] = __ldg(a.y + (int64_t)(c0 + min(c, ncc - 1)) * a.M + ix.w);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) yv[c] = c < ncc ? yl[c] : make_float2(0.f, 0.f);
             atomicAdd(&s_cnt[my_row], 1);
         }
     }
@@ -594,9 +596,11 @@ __global__ void __launch_bounds__(512) k_spread_rows(SpreadArgs a) {
 #pragma unroll
         for (int q = 0; q < D * J; ++q) w[q] = __ldg(pw + q);
         float2* yv = s_y + (size_t)slot * YP;
+        float2 yl[CPT];   // all coil loads in flight at once (clamped coil, zero past the chunk)
 #pragma unroll
-        for (int c = 0; c < CPT; ++c)
-            yv[c] = c < ncc ? __ldg(a.y + (int64_t)(c0 + c) * a.M + ix.w) : make_float2(0.f, 0.f);
+        for (int c = 0; c < CPT; ++c) yl[c] = __ldg(a.y + (int64_t)(c0 + min(c, ncc - 1)) * a.M + ix.w);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) yv[c] = c < ncc ? yl[c] : make_float2(0.f, 0.f);
         atomicAdd(&s_cur[bk], 1);
     }
     __syncthreads();
