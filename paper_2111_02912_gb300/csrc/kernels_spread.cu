@@ -635,50 +635,109 @@ __global__ void __launch_bounds__(512) k_spread_rows(SpreadArgs a) {
     const int c = lane & (CPT - 1), jg = lane / CPT;
     const int nseg = R >= NW ? 1 : (NW + R - 1) / R;   // row segments when rows are fewer than warps
     const int segw = (Bl + nseg - 1) / nseg;
-    for (int u = warp; u < R * nseg; u += NW) {
-        const int r = u / nseg, sg = u - r * nseg;
-        const int x_lo = sg * segw, x_hi = min(Bl, x_lo + segw);
-        int l0 = r, l1 = 0;
-        if (D == 3) {
-            l0 = r / Bt[1];
-            l1 = r - l0 * Bt[1];
-        }
-        float2* arow = s_acc + (size_t)r * Bl * CPT + c;
-#pragma unroll 1
-        for (int a0 = 0; a0 < J; ++a0) {
-#pragma unroll 1
-            for (int a1 = 0; a1 < (D > 2 ? J : 1); ++a1) {
-                const int b = D == 2 ? l0 + a0 : (l0 + a0) * E[1] + (l1 + a1);
-                const int h1 = s_off[b + 1];
-                for (int hh = s_off[b]; hh < h1; ++hh) {
-                    const int h = s_list[hh];
-                    const float* w = s_w + h * WP;
-                    float wo = w[J - 1 - a0];
-                    if (D > 2) wo *= w[J + J - 1 - a1];
-                    const float2 yv = s_y[(size_t)h * YP + c];
-                    const int sl = s_el[h];
+    if constexpr (D == 2) {
+        // The points covering tile row r are those of buckets r .. r + J - 1: one contiguous
+        // range of the sorted hit list, with outer tap J - 1 - (bucket - r).  The loop is
+        // software-pipelined: the next point's metadata is read (from arrays this phase never
+        // writes) before the current point's cells are updated.
+        for (int u = warp; u < R * nseg; u += NW) {
+            const int r = u / nseg, sg = u - r * nseg;
+            const int x_lo = sg * segw, x_hi = min(Bl, x_lo + segw);
+            const int hb = s_off[r], he = s_off[r + J];
+            if (hb >= he) continue;
+            float2* arow = s_acc + (size_t)r * Bl * CPT + c;
+            int hx = s_list[hb];
+            float won = s_w[hx * WP + J - 1 - (s_bk[hx] - r)];
+            float2 yn = s_y[(size_t)hx * YP + c];
+            int sln = s_el[hx];
+            float wxn[NJX];
 #pragma unroll
-                    for (int k = 0; k < NJX; ++k) {
-                        const int jx = jg + k * JPL;
-                        const int col = sl + jx;
-                        if (jx < J && col >= x_lo && col < x_hi) {
-                            const float wt = wo * w[(D - 1) * J + jx];
-                            float2* t = arow + col * CPT;
-                            float2 v = *t;
-                            v.x = fmaf(wt, yv.x, v.x);
-                            v.y = fmaf(wt, yv.y, v.y);
-                            *t = v;
-                        }
+            for (int k = 0; k < NJX; ++k) wxn[k] = s_w[hx * WP + J + min(jg + k * JPL, J - 1)];
+            for (int hh = hb; hh < he; ++hh) {
+                const float wo = won;
+                const float2 yv = yn;
+                const int sl = sln;
+                float wx[NJX];
+#pragma unroll
+                for (int k = 0; k < NJX; ++k) wx[k] = wxn[k];
+                hx = s_list[min(hh + 1, he - 1)];
+                won = s_w[hx * WP + J - 1 - (s_bk[hx] - r)];
+                yn = s_y[(size_t)hx * YP + c];
+                sln = s_el[hx];
+#pragma unroll
+                for (int k = 0; k < NJX; ++k) wxn[k] = s_w[hx * WP + J + min(jg + k * JPL, J - 1)];
+#pragma unroll
+                for (int k = 0; k < NJX; ++k) {
+                    const int jx = jg + k * JPL;
+                    const int col = sl + jx;
+                    if (jx < J && col >= x_lo && col < x_hi) {
+                        const float wt = wo * wx[k];
+                        float2* t = arow + col * CPT;
+                        float2 v = *t;
+                        v.x = fmaf(wt, yv.x, v.x);
+                        v.y = fmaf(wt, yv.y, v.y);
+                        *t = v;
                     }
-                    __syncwarp();   // the next point's cells may be another lane's
+                }
+                __syncwarp();   // the next point's cells may be another lane's
+            }
+        }
+    } else {
+        for (int u = warp; u < R * nseg; u += NW) {
+            const int r = u / nseg, sg = u - r * nseg;
+            const int x_lo = sg * segw, x_hi = min(Bl, x_lo + segw);
+            int l0 = r, l1 = 0;
+            if (D == 3) {
+                l0 = r / Bt[1];
+                l1 = r - l0 * Bt[1];
+            }
+            float2* arow = s_acc + (size_t)r * Bl * CPT + c;
+#pragma unroll 1
+            for (int a0 = 0; a0 < J; ++a0) {
+#pragma unroll 1
+                for (int a1 = 0; a1 < (D > 2 ? J : 1); ++a1) {
+                    const int b = D == 2 ? l0 + a0 : (l0 + a0) * E[1] + (l1 + a1);
+                    const int h1 = s_off[b + 1];
+                    for (int hh = s_off[b]; hh < h1; ++hh) {
+                        const int h = s_list[hh];
+                        const float* w = s_w + h * WP;
+                        float wo = w[J - 1 - a0];
+                        if (D > 2) wo *= w[J + J - 1 - a1];
+                        const float2 yv = s_y[(size_t)h * YP + c];
+                        const int sl = s_el[h];
+#pragma unroll
+                        for (int k = 0; k < NJX; ++k) {
+                            const int jx = jg + k * JPL;
+                            const int col = sl + jx;
+                            if (jx < J && col >= x_lo && col < x_hi) {
+                                const float wt = wo * w[(D - 1) * J + jx];
+                                float2* t = arow + col * CPT;
+                                float2 v = *t;
+                                v.x = fmaf(wt, yv.x, v.x);
+                                v.y = fmaf(wt, yv.y, v.y);
+                                *t = v;
+                            }
+                        }
+                        __syncwarp();   // the next point's cells may be another lane's
+                    }
                 }
             }
         }
     }
-    __syncthreads();
+    __syncthreads();   // every warp's rows are complete
 
     // write the tile coil-fastest: a tile row is Bt_last cells, contiguous in the grid
     const int K1 = D > 1 ? Kd[1] : 1, K2 = D > 2 ? Kd[2] : 1;
+    if (D == 2 && nparts == 1 && ncc == CPT && a.C == CPT) {
+        // all coils in this block: each tile row is one contiguous run of Bl * CPT complex
+        const int per_row4 = Bl * CPT / 2;
+        for (int row = warp; row < R; row += NW) {
+            const float4* src = (const float4*)(s_acc + (size_t)row * Bl * CPT);
+            float4* dst = (float4*)(a.grid + ((int64_t)(org[0] + row) * K1 + org[1]) * CPT);
+            for (int i = lane; i < per_row4; i += 32) dst[i] = src[i];
+        }
+        return;
+    }
     const int rowlen = Bl * ncc;
     const uint32_t mg = ncc > 1 ? (uint32_t)((((uint64_t)1 << 32) + ncc - 1) / ncc) : 0u;
     for (int f = tid; f < R * rowlen; f += nt) {
