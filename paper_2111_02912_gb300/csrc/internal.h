@@ -26,6 +26,7 @@ struct SortArgs {
     int* offsets;     // [nbins + 1]  first sorted point of each bin
     int* item_off;    // [nbins + 1]  first spread work item of each tile
     int* tile_parts;  // [nbins]      spread work items of each tile
+    int* heavy;       // [nbins + 1]  count, then the tiles with more than one work item (any order)
     int* tile_nbr;    // [nbins][kNbrStride]  bins that reach the tile: count, then (start, prefix) pairs
     int4* items;      // [max_items]  {tile, part, nparts, 0}
     int* nitems;      // [1]
@@ -174,6 +175,7 @@ struct SpreadArgs {
     const int4* items;    // spread work items {tile, part, nparts, candidates}
     const int* nitems;
     const int* tile_parts;
+    const int* heavy;     // [nbins + 1]: count, then the tiles split over several work items
     int max_items, P;
     const float2* y;      // [C][M]
     int64_t M;

@@ -132,7 +132,10 @@ __global__ void __launch_bounds__(1024) k_bin_scan(SortArgs a) {
         a.kcount[b] = 0;
         excl += v;
     }
-    if (threadIdx.x == 0) a.offsets[n] = (int)a.m;
+    if (threadIdx.x == 0) {
+        a.offsets[n] = (int)a.m;
+        a.heavy[0] = 0;
+    }
 }
 
 // Per tile: the bins that can reach it (its own and those holding the J-1
@@ -172,6 +175,7 @@ __global__ void __launch_bounds__(1024) k_item_scan(SortArgs a) {
         const int parts = a.tile_parts[b];
         a.item_off[b] = excl;
         for (int k = 0; k < parts; ++k) a.items[excl + k] = make_int4(b, k, parts, 0);
+        if (parts > 1) a.heavy[1 + atomicAdd(a.heavy, 1)] = b;
         excl += parts;
     }
     if (threadIdx.x == 0) {
@@ -197,7 +201,10 @@ __global__ void __launch_bounds__(1024) k_sort_tables(SortArgs a) {
         a.kcount[b] = 0;
         excl += v;
     }
-    if (t == 0) a.offsets[n] = (int)a.m;
+    if (t == 0) {
+        a.offsets[n] = (int)a.m;
+        a.heavy[0] = 0;
+    }
     __syncthreads();   // offsets are read by other threads below (global, same block)
     int parts_sum = 0;
     int nbr[27];
@@ -223,6 +230,7 @@ __global__ void __launch_bounds__(1024) k_sort_tables(SortArgs a) {
         const int parts = a.tile_parts[b];
         a.item_off[b] = excl;
         for (int k = 0; k < parts; ++k) a.items[excl + k] = make_int4(b, k, parts, 0);
+        if (parts > 1) a.heavy[1 + atomicAdd(a.heavy, 1)] = b;
         excl += parts;
     }
     if (t == 0) {

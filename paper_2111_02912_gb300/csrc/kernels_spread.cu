@@ -804,24 +804,31 @@ cudaError_t launch_spread_cells(const SpreadArgs& a, cudaStream_t s) {
 }
 
 // Clears the cells (all coils) of the tiles that are split over several work items.
+// The sort lists these tiles; blocks walk the list, warps take tile rows (all axes but the
+// last), and each row's cells times coils are one contiguous run of the grid.
 __global__ void k_zero_heavy_tiles(SpreadArgs a) {
-    const int tile = blockIdx.x;
-    if (a.tile_parts[tile] <= 1) return;
-    int r = tile, org[kMaxDim] = {0, 0, 0}, Bt[kMaxDim] = {1, 1, 1}, Kd[kMaxDim] = {1, 1, 1};
-    for (int d = a.D - 1; d >= 0; --d) {
-        const int bc = r % a.nb[d];
-        r /= a.nb[d];
-        Kd[d] = a.K[d];
-        org[d] = bc * a.B[d];
-        Bt[d] = min(a.B[d], Kd[d] - org[d]);
-    }
-    const int n = Bt[0] * Bt[1] * Bt[2] * a.C;
-    for (int f = threadIdx.x; f < n; f += blockDim.x) {
-        const int c = f % a.C, cell = f / a.C;
-        const int l2 = cell % Bt[2], q = cell / Bt[2];
-        const int l1 = q % Bt[1], l0 = q / Bt[1];
-        const int64_t gcell = ((int64_t)(org[0] + l0) * Kd[1] + (org[1] + l1)) * Kd[2] + (org[2] + l2);
-        a.grid[gcell * a.C + c] = make_float2(0.f, 0.f);
+    const int nh = a.heavy[0];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = blockIdx.x; i < nh; i += gridDim.x) {
+        int r = a.heavy[1 + i], org[kMaxDim] = {0, 0, 0}, Bt[kMaxDim] = {1, 1, 1}, Kd[kMaxDim] = {1, 1, 1};
+        for (int d = a.D - 1; d >= 0; --d) {
+            const int bc = r % a.nb[d];
+            r /= a.nb[d];
+            Kd[d] = a.K[d];
+            org[d] = bc * a.B[d];
+            Bt[d] = min(a.B[d], Kd[d] - org[d]);
+        }
+        const int Dl = a.D - 1;
+        const int rows = a.D == 1 ? 1 : (a.D == 2 ? Bt[0] : Bt[0] * Bt[1]);
+        const int run = Bt[Dl] * a.C;
+        for (int row = warp; row < rows; row += nw) {
+            int64_t cell0;
+            if (a.D == 1) cell0 = org[0];
+            else if (a.D == 2) cell0 = (int64_t)(org[0] + row) * Kd[1] + org[1];
+            else cell0 = ((int64_t)(org[0] + row / Bt[1]) * Kd[1] + (org[1] + row % Bt[1])) * Kd[2] + org[2];
+            float2* dst = a.grid + cell0 * a.C;
+            for (int f = lane; f < run; f += 32) dst[f] = make_float2(0.f, 0.f);
+        }
     }
 }
 
@@ -863,7 +870,7 @@ cudaError_t launch_spread(const SpreadArgs& a, int /*cpl*/, cudaStream_t s, size
 }
 
 cudaError_t launch_zero_heavy_tiles(const SpreadArgs& a, cudaStream_t s) {
-    k_zero_heavy_tiles<<<a.nbins, 256, 0, s>>>(a);
+    k_zero_heavy_tiles<<<std::min(a.nbins, 152 * 4), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

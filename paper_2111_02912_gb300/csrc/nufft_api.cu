@@ -87,6 +87,7 @@ struct nufft_plan_s {
     int* d_offsets = nullptr;
     int* d_item_off = nullptr;
     int* d_tile_parts = nullptr;
+    int* d_heavy = nullptr;
     int* d_tile_nbr = nullptr;
     int* d_nitems = nullptr;
     int4* d_items = nullptr;
@@ -176,7 +177,7 @@ double kb_ft(double f, int J, double beta) {
 
 void free_plan(nufft_plan_s* p) {
     for (int d = 0; d < 3; ++d) { cudaFree(p->d_deap[d]); cudaFree(p->d_tw[d]); }
-    cudaFree(p->d_kcount); cudaFree(p->d_offsets); cudaFree(p->d_item_off); cudaFree(p->d_tile_parts); cudaFree(p->d_tile_nbr);
+    cudaFree(p->d_kcount); cudaFree(p->d_offsets); cudaFree(p->d_item_off); cudaFree(p->d_tile_parts); cudaFree(p->d_heavy); cudaFree(p->d_tile_nbr);
     cudaFree(p->d_nitems); cudaFree(p->d_items); cudaFree(p->d_local); cudaFree(p->d_keyid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
     cudaFree(p->d_pw);
     cudaFree(p->d_G); cudaFree(p->d_T);
@@ -332,6 +333,7 @@ SortArgs sort_args(nufft_plan_s* p, const float* omega) {
     a.offsets = p->d_offsets;
     a.item_off = p->d_item_off;
     a.tile_parts = p->d_tile_parts;
+    a.heavy = p->d_heavy;
     a.tile_nbr = p->d_tile_nbr;
     a.items = p->d_items;
     a.nitems = p->d_nitems;
@@ -399,8 +401,9 @@ Tile pick_tile(int L, int64_t B, int64_t S, bool coil_sum, int n_out) {
     Tile t{};
     if (fft2_factor(L, t.L1, t.L2)) {
         // 8 adjacent lines (64-byte segments along the channel axis), two blocks per SM:
-        // measured faster than 4 or 16 lines on the 640-point passes
-        int TL = 8;
+        // measured faster than 4 or 16 lines on the 640-point passes.  The coil-summing last
+        // inverse pass takes up to 16 coils per block, so 16 coils need no partial-sum pass.
+        int TL = (coil_sum && S > 8) ? 16 : 8;
         t.TS = std::min<int>(TL, pow2_ceil(S));
         t.TB = std::min<int>(TL / t.TS, pow2_ceil(B));
         t.TL = t.TB * t.TS;
@@ -512,6 +515,7 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
     sa.items = p->d_items;
     sa.nitems = p->d_nitems;
     sa.tile_parts = p->d_tile_parts;
+    sa.heavy = p->d_heavy;
     sa.max_items = (int)max_items(*p, p->M);
     sa.P = p->P;
     sa.y = y;
@@ -637,7 +641,7 @@ size_t nufft_workspace_bytes(const nufft_opts* o, int64_t m) {
     size_t G, T;
     workspace_elems(p, G, T);
     size_t b = (G + T) * sizeof(float2) + point_bytes(p, std::max<int64_t>(m, 1));
-    b += (size_t)((4 + kNbrStride) * p.nbins + 6) * sizeof(int);
+    b += (size_t)((5 + kNbrStride) * p.nbins + 7) * sizeof(int);
     for (int d = 0; d < p.D; ++d) b += (size_t)p.N[d] * sizeof(float) + (size_t)p.K[d] * sizeof(float2);
     return b;
 }
@@ -676,6 +680,7 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
         cudaMalloc(&p->d_offsets, sizeof(int) * (p->nbins + 1)) != cudaSuccess ||
         cudaMalloc(&p->d_item_off, sizeof(int) * (p->nbins + 1)) != cudaSuccess ||
         cudaMalloc(&p->d_tile_parts, sizeof(int) * p->nbins) != cudaSuccess ||
+        cudaMalloc(&p->d_heavy, sizeof(int) * (p->nbins + 1)) != cudaSuccess ||
         cudaMalloc(&p->d_tile_nbr, sizeof(int) * kNbrStride * p->nbins) != cudaSuccess ||
         cudaMalloc(&p->d_nitems, sizeof(int)) != cudaSuccess)
         return oom("bins");
@@ -914,6 +919,7 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
     const size_t o_kcount = cv.take<int>(p.nbins),
                  o_offsets = cv.take<int>(p.nbins + 1),
                  o_item_off = cv.take<int>(p.nbins + 1), o_tile_parts = cv.take<int>(p.nbins),
+                 o_heavy = cv.take<int>(p.nbins + 1),
                  o_tile_nbr = cv.take<int>((size_t)kNbrStride * p.nbins),
                  o_nitems = cv.take<int>(1), o_items = cv.take<int4>(max_items(p, mc)), o_local = cv.take<int>(mc),
                  o_keyid = cv.take<int>(mc), o_pidx = cv.take<int4>(mc), o_pfrac = cv.take<float4>(mc),
@@ -949,6 +955,7 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
     p.d_offsets = (int*)(b + o_offsets);
     p.d_item_off = (int*)(b + o_item_off);
     p.d_tile_parts = (int*)(b + o_tile_parts);
+    p.d_heavy = (int*)(b + o_heavy);
     p.d_tile_nbr = (int*)(b + o_tile_nbr);
     p.d_nitems = (int*)(b + o_nitems);
     p.d_items = (int4*)(b + o_items);
