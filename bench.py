@@ -324,9 +324,13 @@ def traffic_for(kernel):
 
 
 def source_hash():
+    """Hash of every kernel source: a committed traffic figure applies only to the sources it was taken on."""
     h = hashlib.sha256()
-    for name in ("kernels_fft.cu", "kernels_interp.cu", "kernels_sort.cu", "common.cuh", "nufft_api.cu"):
-        h.update(open(os.path.join(ROOT, "paper_2111_02912_gb300", "csrc", name), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2111_02912_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
 
