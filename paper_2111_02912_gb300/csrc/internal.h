@@ -177,7 +177,8 @@ struct SpreadArgs {
     const int* tile_parts;
     const int* heavy;     // [nbins + 1]: count, then the tiles split over several work items
     int max_items, P;
-    const float2* y;      // [C][M]
+    const float2* y;      // [C][M], by original index, or by sorted position when y_sorted
+    int y_sorted;
     int64_t M;
     int C, CC;            // coils, coils per block
     int G, lgG;           // tap slots per warp (lanes = G slots x 32/G coils)
@@ -186,6 +187,8 @@ struct SpreadArgs {
 };
 cudaError_t launch_spread(const SpreadArgs& a, int cpl, cudaStream_t s, size_t smem);
 cudaError_t launch_zero_heavy_tiles(const SpreadArgs& a, cudaStream_t s);
+// ys[c][i] = y[c][idx[i].w]: the coil values in sorted point order (coalesced reads in the spread).
+cudaError_t launch_permute_y(const int4* idx, const float2* y, float2* ys, int64_t M, int C, cudaStream_t s);
 int spread_min_slots(int D, int J);   // fewest tap slots per warp the spread kernel supports
 // Tile spread (row owners in 2-D, cell owners in 3-D): D in {2, 3}, every tile edge <= K - J + 1 and >= J - 1, prod B <= 512,
 // a.CC = coils per block (4, 8 or 16), a.P candidates per work item (<= prod B).

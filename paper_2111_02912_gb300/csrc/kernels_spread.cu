@@ -345,7 +345,8 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
             float2* yv = s_y + (size_t)my_slot * (CPT + 1);
             float2 yl[CPT];   // all coil loads in flight at once (clamped coil, zero past the chunk)
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) yl[c] = __ldg(a.y + (int64_t)(c0 + min(c, ncc - 1)) * a.M + ix.w);
+            for (int c = 0; c < CPT; ++c)
+                yl[c] = __ldg(a.y + (int64_t)(c0 + min(c, ncc - 1)) * a.M + (a.y_sorted ? p : (int64_t)ix.w));
 #pragma unroll
             for (int c = 0; c < CPT; ++c) yv[c] = c < ncc ? yl[c] : make_float2(0.f, 0.f);
             atomicAdd(&s_cnt[my_row], 1);
@@ -576,6 +577,17 @@ __global__ void __launch_bounds__(512) k_spread_rows(SpreadArgs a) {
         while (q + 1 < nn && s_pref[q + 1] <= cand) ++q;
         const int64_t pidx = s_start[q] + (cand - s_pref[q]);
         const int4 ix = a.pts.idx[pidx];
+        // weights and (sorted) coil values are loaded with the record, before the window test, so
+        // that staging takes one memory round trip; a miss wastes these reads
+        float wv[D * J];
+        const float* pw = a.pts.w + pidx * a.pts.ws;
+#pragma unroll
+        for (int q = 0; q < D * J; ++q) wv[q] = __ldg(pw + q);
+        float2 yl[CPT];   // clamped coil, zero past the chunk
+        if (a.y_sorted) {
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) yl[c] = __ldg(a.y + (int64_t)(c0 + min(c, ncc - 1)) * a.M + pidx);
+        }
         bool hit = true;
         int e[kMaxDim] = {0, 0, 0};
 #pragma unroll
@@ -587,18 +599,18 @@ __global__ void __launch_bounds__(512) k_spread_rows(SpreadArgs a) {
             e[d] = sd + J - 1;
         }
         if (!hit) continue;
+        if (!a.y_sorted) {
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) yl[c] = __ldg(a.y + (int64_t)(c0 + min(c, ncc - 1)) * a.M + ix.w);
+        }
         const int slot = atomicAdd(&s_nh, 1);
         const int bk = D == 2 ? e[0] : e[0] * E[1] + e[1];
         s_el[slot] = e[D - 1] - (J - 1);               // window start along the last axis, tile-relative
         s_bk[slot] = bk;
-        const float* pw = a.pts.w + pidx * a.pts.ws;
         float* w = s_w + slot * WP;
 #pragma unroll
-        for (int q = 0; q < D * J; ++q) w[q] = __ldg(pw + q);
+        for (int q = 0; q < D * J; ++q) w[q] = wv[q];
         float2* yv = s_y + (size_t)slot * YP;
-        float2 yl[CPT];   // all coil loads in flight at once (clamped coil, zero past the chunk)
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) yl[c] = __ldg(a.y + (int64_t)(c0 + min(c, ncc - 1)) * a.M + ix.w);
 #pragma unroll
         for (int c = 0; c < CPT; ++c) yv[c] = c < ncc ? yl[c] : make_float2(0.f, 0.f);
         atomicAdd(&s_cur[bk], 1);
@@ -804,6 +816,28 @@ cudaError_t launch_spread_cells(const SpreadArgs& a, cudaStream_t s) {
 }
 
 // Clears the cells (all coils) of the tiles that are split over several work items.
+__global__ void k_permute_y(const int4* __restrict__ idx, const float2* __restrict__ y, float2* __restrict__ ys,
+                            int64_t M, int C) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int64_t o = idx[i].w;
+    int c = 0;
+    for (; c + 4 <= C; c += 4) {   // four independent loads in flight
+        float2 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = __ldg(y + (int64_t)(c + q) * M + o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ys[(int64_t)(c + q) * M + i] = v[q];
+    }
+    for (; c < C; ++c) ys[(int64_t)c * M + i] = __ldg(y + (int64_t)c * M + o);
+}
+
+cudaError_t launch_permute_y(const int4* idx, const float2* y, float2* ys, int64_t M, int C, cudaStream_t s) {
+    if (M == 0) return cudaSuccess;
+    k_permute_y<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(idx, y, ys, M, C);
+    return cudaGetLastError();
+}
+
 // The sort lists these tiles; blocks walk the list, warps take tile rows (all axes but the
 // last), and each row's cells times coils are one contiguous run of the grid.
 __global__ void k_zero_heavy_tiles(SpreadArgs a) {

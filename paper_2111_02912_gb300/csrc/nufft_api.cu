@@ -36,11 +36,11 @@ int fail(int status, const std::string& msg) {
 
 enum ProfKind {
     PK_ZERO, PK_BIN_COUNT, PK_BIN_SCAN, PK_TILE_SCAN, PK_BIN_SCATTER, PK_BIN_ITEMS, PK_FFT_FWD_FIRST, PK_FFT_FWD_MID,
-    PK_FFT_INV_MID, PK_FFT_INV_LAST, PK_GATHER_FWD, PK_GATHER_JVP, PK_GATHER_VJP, PK_ZERO_HEAVY, PK_SPREAD, PK_SUM_CHUNKS, PK_COUNT
+    PK_FFT_INV_MID, PK_FFT_INV_LAST, PK_GATHER_FWD, PK_GATHER_JVP, PK_GATHER_VJP, PK_ZERO_HEAVY, PK_SPREAD, PK_SUM_CHUNKS, PK_PERMUTE_Y, PK_COUNT
 };
 const char* kProfNames[PK_COUNT] = {"zero", "bin_count", "bin_scan", "tile_scan", "bin_scatter", "bin_items", "fft_fwd_first",
                                     "fft_fwd_mid", "fft_inv_mid", "fft_inv_last", "gather_fwd", "gather_jvp",
-                                    "gather_vjp", "zero_heavy", "spread", "sum_chunks"};
+                                    "gather_vjp", "zero_heavy", "spread", "sum_chunks", "permute_y"};
 
 int64_t grid_size(int64_t n, double sigma) {
     int64_t k = (int64_t)std::ceil(sigma * (double)n - 1e-9);
@@ -532,6 +532,15 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
     if ((st = launch(p, PK_ZERO_HEAVY, s, [&] { return launch_zero_heavy_tiles(sa, s); }))) return st;
     if (p->cell_spread) {
         sa.CC = C <= 4 ? 4 : (C <= 8 ? 8 : 16);
+        // y in sorted point order (in T, free until the inverse FFT passes): the tile kernels then
+        // read it coalesced and without waiting for the point record
+        if ((size_t)C * (size_t)p->M <= p->T_elems && p->M > 0) {
+            if ((st = launch(p, PK_PERMUTE_Y, s,
+                             [&] { return launch_permute_y(p->d_pidx, y, p->d_T, p->M, C, s); })))
+                return st;
+            sa.y = p->d_T;
+            sa.y_sorted = 1;
+        }
         if ((st = launch(p, PK_SPREAD, s, [&] { return launch_spread_cells(sa, s); }))) return st;
     } else {
         if ((st = launch(p, PK_SPREAD, s, [&] { return launch_spread(sa, cpl, s, ssm); }))) return st;
