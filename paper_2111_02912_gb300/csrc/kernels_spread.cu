@@ -519,252 +519,289 @@ template <int D, int J, int CPT>
 __global__ void __launch_bounds__(512) k_spread_rows(SpreadArgs a) {
     extern __shared__ float4 smem4[];
     __shared__ int s_start[27], s_pref[28], s_nn, s_nh;
-    const int it = blockIdx.x;
-    if (it >= a.nitems[0]) return;     // block-uniform
+    const int nitems = a.nitems[0];
+    int it = blockIdx.x;
+    if (it >= nitems) return;     // block-uniform
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = nt >> 5;
-    const int4 item = a.items[it];
-    const int tile = item.x, part = item.y, nparts = item.z;
-    int org[kMaxDim] = {0, 0, 0}, Bt[kMaxDim] = {1, 1, 1}, Kd[kMaxDim] = {1, 1, 1}, E[kMaxDim] = {1, 1, 1};
+    // Persistent: the block walks items it, it + gridDim.x, ...  The next item's descriptor and
+    // its tile's bin list are loaded while the current item is processed (two dependent global
+    // round trips that would otherwise open every item).
+    int4 item = a.items[it];
+    int tn0 = 0, tn1 = 0, tn2 = 0;   // this thread's entries of the tile's bin list
     {
-        int r = tile;
-        for (int d = D - 1; d >= 0; --d) {
-            const int nbd = a.nb[d];
-            const int bc = r % nbd;
-            r /= nbd;
-            Kd[d] = a.K[d];
-            org[d] = bc * a.B[d];
-            Bt[d] = min(a.B[d], Kd[d] - org[d]);
-            E[d] = Bt[d] + J - 1;
-        }
+        const int* tn = a.tile_nbr + (int64_t)item.x * kNbrStride;
+        if (tid == 0) tn0 = tn[0];
+        if (tid < 27) tn1 = tn[1 + 2 * tid];
+        if (tid < 28) tn2 = tn[2 + 2 * tid];
     }
-    const int NB = D == 2 ? E[0] : E[0] * E[1];   // buckets
-    const int P = a.P;
-    const int c0 = blockIdx.y * CPT;
-    const int ncc = min(CPT, a.C - c0);
-    const int tcells = Bt[0] * Bt[1] * Bt[2];
-    const int Bl = Bt[D - 1];
-    const int R = tcells / Bl;                    // tile rows
-    // shared: tile [tcells][CPT], y [P][YP], weights [P][WP], last start e_l [P], bucket [P],
-    // sorted hits [P], bucket offsets [NB + 1], cursors [NB]; odd row pitches YP, WP keep the
-    // one-candidate-per-thread staging stores on distinct banks
-    constexpr int YP = CPT + 1, WP = D * J + ((D * J + 1) & 1);
-    float2* s_acc = (float2*)smem4;
-    float2* s_y = s_acc + (size_t)tcells * CPT;
-    float* s_w = (float*)(s_y + (size_t)P * YP);
-    int* s_el = (int*)(s_w + P * WP);
-    int* s_bk = s_el + P;
-    int* s_list = s_bk + P;
-    int* s_off = s_list + P;
-    int* s_cur = s_off + NB + 1;
-
-    {
-        const int* tn = a.tile_nbr + (int64_t)tile * kNbrStride;
-        if (tid == 0) { s_nn = tn[0]; s_nh = 0; }
-        if (tid < 27) s_start[tid] = tn[1 + 2 * tid];      // entries past the count are never used
-        if (tid < 28) s_pref[tid] = tn[2 + 2 * tid];
-    }
-    for (int i = tid; i < tcells * CPT; i += nt) s_acc[i] = make_float2(0.f, 0.f);
-    for (int i = tid; i < NB; i += nt) s_cur[i] = 0;
-    __syncthreads();
-
-    // ------------------------------------------------ stage and count the hits
-    const int nn = s_nn;
-    const int lo = part * P, hi = min(s_pref[nn], lo + P);
-    for (int t = tid; t < P; t += nt) {
-        const int cand = lo + t;
-        if (cand >= hi) break;
-        int q = 0;
-        while (q + 1 < nn && s_pref[q + 1] <= cand) ++q;
-        const int64_t pidx = s_start[q] + (cand - s_pref[q]);
-        const int4 ix = a.pts.idx[pidx];
-        // weights and (sorted) coil values are loaded with the record, before the window test, so
-        // that staging takes one memory round trip; a miss wastes these reads
-        float wv[D * J];
-        const float* pw = a.pts.w + pidx * a.pts.ws;
-#pragma unroll
-        for (int q = 0; q < D * J; ++q) wv[q] = __ldg(pw + q);
-        float2 yl[CPT];   // clamped coil, zero past the chunk
-        if (a.y_sorted) {
-#pragma unroll
-            for (int c = 0; c < CPT; ++c) yl[c] = __ldg(a.y + (int64_t)(c0 + min(c, ncc - 1)) * a.M + pidx);
-        }
-        bool hit = true;
-        int e[kMaxDim] = {0, 0, 0};
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            int sd = (d == 0 ? ix.x : (d == 1 ? ix.y : ix.z)) - org[d];
-            if (sd < 0) sd += Kd[d];
-            if (sd > Kd[d] - J) sd -= Kd[d];           // starts up to J-1 cells before the tile
-            hit = hit && sd >= -(J - 1) && sd < Bt[d];
-            e[d] = sd + J - 1;
-        }
-        if (!hit) continue;
-        if (!a.y_sorted) {
-#pragma unroll
-            for (int c = 0; c < CPT; ++c) yl[c] = __ldg(a.y + (int64_t)(c0 + min(c, ncc - 1)) * a.M + ix.w);
-        }
-        const int slot = atomicAdd(&s_nh, 1);
-        const int bk = D == 2 ? e[0] : e[0] * E[1] + e[1];
-        s_el[slot] = e[D - 1] - (J - 1);               // window start along the last axis, tile-relative
-        s_bk[slot] = bk;
-        float* w = s_w + slot * WP;
-#pragma unroll
-        for (int q = 0; q < D * J; ++q) w[q] = wv[q];
-        float2* yv = s_y + (size_t)slot * YP;
-#pragma unroll
-        for (int c = 0; c < CPT; ++c) yv[c] = c < ncc ? yl[c] : make_float2(0.f, 0.f);
-        atomicAdd(&s_cur[bk], 1);
-    }
-    __syncthreads();
-    // exclusive scan of the bucket counts (one warp)
-    if (warp == 0) {
-        int carry = 0;
-        for (int b0 = 0; b0 < NB; b0 += 32) {
-            const int b = b0 + lane;
-            const int v = b < NB ? s_cur[b] : 0;
-            int incl = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += u;
+    for (;;) {
+        const int itn = it + (int)gridDim.x;
+        int4 itemn = make_int4(0, 0, 0, 0);
+        if (itn < nitems) itemn = a.items[itn];
+        const int tile = item.x, part = item.y, nparts = item.z;
+        int org[kMaxDim] = {0, 0, 0}, Bt[kMaxDim] = {1, 1, 1}, Kd[kMaxDim] = {1, 1, 1}, E[kMaxDim] = {1, 1, 1};
+        {
+            int r = tile;
+            for (int d = D - 1; d >= 0; --d) {
+                const int nbd = a.nb[d];
+                const int bc = r % nbd;
+                r /= nbd;
+                Kd[d] = a.K[d];
+                org[d] = bc * a.B[d];
+                Bt[d] = min(a.B[d], Kd[d] - org[d]);
+                E[d] = Bt[d] + J - 1;
             }
-            if (b < NB) {
-                s_off[b] = carry + incl - v;
-                s_cur[b] = carry + incl - v;
-            }
-            carry += __shfl_sync(0xffffffffu, incl, 31);
         }
-        if (lane == 0) s_off[NB] = carry;
-    }
-    __syncthreads();
-    const int nh = s_nh;
-    for (int h = tid; h < nh; h += nt) s_list[atomicAdd(&s_cur[s_bk[h]], 1)] = h;
-    __syncthreads();
+        const int NB = D == 2 ? E[0] : E[0] * E[1];   // buckets
+        const int P = a.P;
+        const int c0 = blockIdx.y * CPT;
+        const int ncc = min(CPT, a.C - c0);
+        const int tcells = Bt[0] * Bt[1] * Bt[2];
+        const int Bl = Bt[D - 1];
+        const int R = tcells / Bl;                    // tile rows
+        // shared: tile [tcells][CPT], y [P][YP], weights [P][WP], last start e_l [P], bucket [P],
+        // sorted hits [P], bucket offsets [NB + 1], cursors [NB]; odd row pitches YP, WP keep the
+        // one-candidate-per-thread staging stores on distinct banks
+        constexpr int YP = CPT + 1, WP = D * J + ((D * J + 1) & 1);
+        float2* s_acc = (float2*)smem4;
+        float2* s_y = s_acc + (size_t)tcells * CPT;
+        float* s_w = (float*)(s_y + (size_t)P * YP);
+        int* s_el = (int*)(s_w + P * WP);
+        int* s_bk = s_el + P;
+        int* s_list = s_bk + P;
+        int* s_off = s_list + P;
+        int* s_cur = s_off + NB + 1;
 
-    // ------------------------------------------------------------- accumulate
-    constexpr int JPL = 32 / CPT;                 // last-axis taps per lane pass
-    constexpr int NJX = (J + JPL - 1) / JPL;      // passes
-    const int c = lane & (CPT - 1), jg = lane / CPT;
-    const int nseg = R >= NW ? 1 : (NW + R - 1) / R;   // row segments when rows are fewer than warps
-    const int segw = (Bl + nseg - 1) / nseg;
-    if constexpr (D == 2) {
-        // The points covering tile row r are those of buckets r .. r + J - 1: one contiguous
-        // range of the sorted hit list, with outer tap J - 1 - (bucket - r).  The loop is
-        // software-pipelined: the next point's metadata is read (from arrays this phase never
-        // writes) before the current point's cells are updated.
-        for (int u = warp; u < R * nseg; u += NW) {
-            const int r = u / nseg, sg = u - r * nseg;
-            const int x_lo = sg * segw, x_hi = min(Bl, x_lo + segw);
-            const int hb = s_off[r], he = s_off[r + J];
-            if (hb >= he) continue;
-            float2* arow = s_acc + (size_t)r * Bl * CPT + c;
-            int hx = s_list[hb];
-            float won = s_w[hx * WP + J - 1 - (s_bk[hx] - r)];
-            float2 yn = s_y[(size_t)hx * YP + c];
-            int sln = s_el[hx];
-            float wxn[NJX];
+        if (tid == 0) { s_nn = tn0; s_nh = 0; }
+        if (tid < 27) s_start[tid] = tn1;      // entries past the count are never used
+        if (tid < 28) s_pref[tid] = tn2;
+        for (int i = tid; i < tcells * CPT; i += nt) s_acc[i] = make_float2(0.f, 0.f);
+        for (int i = tid; i < NB; i += nt) s_cur[i] = 0;
+        __syncthreads();
+
+        // ------------------------------------------------ stage and count the hits
+        const int nn = s_nn;
+        const int lo = part * P, hi = min(s_pref[nn], lo + P);
+        for (int t = tid; t < P; t += nt) {
+            const int cand = lo + t;
+            if (cand >= hi) break;
+            int q = 0;
+            while (q + 1 < nn && s_pref[q + 1] <= cand) ++q;
+            const int64_t pidx = s_start[q] + (cand - s_pref[q]);
+            const int4 ix = a.pts.idx[pidx];
+            // weights and (sorted) coil values are loaded with the record, before the window test, so
+            // that staging takes one memory round trip; a miss wastes these reads
+            float wv[D * J];
+            const float* pw = a.pts.w + pidx * a.pts.ws;
 #pragma unroll
-            for (int k = 0; k < NJX; ++k) wxn[k] = s_w[hx * WP + J + min(jg + k * JPL, J - 1)];
-            for (int hh = hb; hh < he; ++hh) {
-                const float wo = won;
-                const float2 yv = yn;
-                const int sl = sln;
-                float wx[NJX];
+            for (int q = 0; q < D * J; ++q) wv[q] = __ldg(pw + q);
+            float2 yl[CPT];   // clamped coil, zero past the chunk
+            if (a.y_sorted) {
 #pragma unroll
-                for (int k = 0; k < NJX; ++k) wx[k] = wxn[k];
-                hx = s_list[min(hh + 1, he - 1)];
-                won = s_w[hx * WP + J - 1 - (s_bk[hx] - r)];
-                yn = s_y[(size_t)hx * YP + c];
-                sln = s_el[hx];
+                for (int c = 0; c < CPT; ++c) yl[c] = __ldg(a.y + (int64_t)(c0 + min(c, ncc - 1)) * a.M + pidx);
+            }
+            bool hit = true;
+            int e[kMaxDim] = {0, 0, 0};
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                int sd = (d == 0 ? ix.x : (d == 1 ? ix.y : ix.z)) - org[d];
+                if (sd < 0) sd += Kd[d];
+                if (sd > Kd[d] - J) sd -= Kd[d];           // starts up to J-1 cells before the tile
+                hit = hit && sd >= -(J - 1) && sd < Bt[d];
+                e[d] = sd + J - 1;
+            }
+            if (!hit) continue;
+            if (!a.y_sorted) {
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) yl[c] = __ldg(a.y + (int64_t)(c0 + min(c, ncc - 1)) * a.M + ix.w);
+            }
+            const int slot = atomicAdd(&s_nh, 1);
+            const int bk = D == 2 ? e[0] : e[0] * E[1] + e[1];
+            s_el[slot] = e[D - 1] - (J - 1);               // window start along the last axis, tile-relative
+            s_bk[slot] = bk;
+            float* w = s_w + slot * WP;
+#pragma unroll
+            for (int q = 0; q < D * J; ++q) w[q] = wv[q];
+            float2* yv = s_y + (size_t)slot * YP;
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) yv[c] = c < ncc ? yl[c] : make_float2(0.f, 0.f);
+            atomicAdd(&s_cur[bk], 1);
+        }
+        if (itn < nitems) {   // the next item's bin list, consumed at its start
+            const int* tn = a.tile_nbr + (int64_t)itemn.x * kNbrStride;
+            if (tid == 0) tn0 = tn[0];
+            if (tid < 27) tn1 = tn[1 + 2 * tid];
+            if (tid < 28) tn2 = tn[2 + 2 * tid];
+        }
+        __syncthreads();
+        // exclusive scan of the bucket counts (one warp)
+        if (warp == 0) {
+            int carry = 0;
+            for (int b0 = 0; b0 < NB; b0 += 32) {
+                const int b = b0 + lane;
+                const int v = b < NB ? s_cur[b] : 0;
+                int incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += u;
+                }
+                if (b < NB) {
+                    s_off[b] = carry + incl - v;
+                    s_cur[b] = carry + incl - v;
+                }
+                carry += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0) s_off[NB] = carry;
+        }
+        __syncthreads();
+        const int nh = s_nh;
+        for (int h = tid; h < nh; h += nt) s_list[atomicAdd(&s_cur[s_bk[h]], 1)] = h;
+        __syncthreads();
+
+        // ------------------------------------------------------------- accumulate
+        constexpr int JPL = 32 / CPT;                 // last-axis taps per lane pass
+        constexpr int NJX = (J + JPL - 1) / JPL;      // passes
+        const int c = lane & (CPT - 1), jg = lane / CPT;
+        const int nseg = R >= NW ? 1 : (NW + R - 1) / R;   // row segments when rows are fewer than warps
+        const int segw = (Bl + nseg - 1) / nseg;
+        if constexpr (D == 2) {
+            // The points covering tile row r are those of buckets r .. r + J - 1: one contiguous
+            // range of the sorted hit list, with outer tap J - 1 - (bucket - r).  The loop is
+            // software-pipelined: the next point's metadata is read (from arrays this phase never
+            // writes) before the current point's cells are updated.
+            for (int u = warp; u < R * nseg; u += NW) {
+                const int r = u / nseg, sg = u - r * nseg;
+                const int x_lo = sg * segw, x_hi = min(Bl, x_lo + segw);
+                const int hb = s_off[r], he = s_off[r + J];
+                if (hb >= he) continue;
+                float2* arow = s_acc + (size_t)r * Bl * CPT + c;
+                int hx = s_list[hb];
+                float won = s_w[hx * WP + J - 1 - (s_bk[hx] - r)];
+                float2 yn = s_y[(size_t)hx * YP + c];
+                int sln = s_el[hx];
+                float wxn[NJX];
 #pragma unroll
                 for (int k = 0; k < NJX; ++k) wxn[k] = s_w[hx * WP + J + min(jg + k * JPL, J - 1)];
+                for (int hh = hb; hh < he; ++hh) {
+                    const float wo = won;
+                    const float2 yv = yn;
+                    const int sl = sln;
+                    float wx[NJX];
 #pragma unroll
-                for (int k = 0; k < NJX; ++k) {
-                    const int jx = jg + k * JPL;
-                    const int col = sl + jx;
-                    if (jx < J && col >= x_lo && col < x_hi) {
-                        const float wt = wo * wx[k];
-                        float2* t = arow + col * CPT;
-                        float2 v = *t;
-                        v.x = fmaf(wt, yv.x, v.x);
-                        v.y = fmaf(wt, yv.y, v.y);
-                        *t = v;
-                    }
-                }
-                __syncwarp();   // the next point's cells may be another lane's
-            }
-        }
-    } else {
-        for (int u = warp; u < R * nseg; u += NW) {
-            const int r = u / nseg, sg = u - r * nseg;
-            const int x_lo = sg * segw, x_hi = min(Bl, x_lo + segw);
-            int l0 = r, l1 = 0;
-            if (D == 3) {
-                l0 = r / Bt[1];
-                l1 = r - l0 * Bt[1];
-            }
-            float2* arow = s_acc + (size_t)r * Bl * CPT + c;
-#pragma unroll 1
-            for (int a0 = 0; a0 < J; ++a0) {
-#pragma unroll 1
-                for (int a1 = 0; a1 < (D > 2 ? J : 1); ++a1) {
-                    const int b = D == 2 ? l0 + a0 : (l0 + a0) * E[1] + (l1 + a1);
-                    const int h1 = s_off[b + 1];
-                    for (int hh = s_off[b]; hh < h1; ++hh) {
-                        const int h = s_list[hh];
-                        const float* w = s_w + h * WP;
-                        float wo = w[J - 1 - a0];
-                        if (D > 2) wo *= w[J + J - 1 - a1];
-                        const float2 yv = s_y[(size_t)h * YP + c];
-                        const int sl = s_el[h];
+                    for (int k = 0; k < NJX; ++k) wx[k] = wxn[k];
+                    hx = s_list[min(hh + 1, he - 1)];
+                    won = s_w[hx * WP + J - 1 - (s_bk[hx] - r)];
+                    yn = s_y[(size_t)hx * YP + c];
+                    sln = s_el[hx];
 #pragma unroll
-                        for (int k = 0; k < NJX; ++k) {
-                            const int jx = jg + k * JPL;
-                            const int col = sl + jx;
-                            if (jx < J && col >= x_lo && col < x_hi) {
-                                const float wt = wo * w[(D - 1) * J + jx];
-                                float2* t = arow + col * CPT;
-                                float2 v = *t;
-                                v.x = fmaf(wt, yv.x, v.x);
-                                v.y = fmaf(wt, yv.y, v.y);
-                                *t = v;
-                            }
+                    for (int k = 0; k < NJX; ++k) wxn[k] = s_w[hx * WP + J + min(jg + k * JPL, J - 1)];
+#pragma unroll
+                    for (int k = 0; k < NJX; ++k) {
+                        const int jx = jg + k * JPL;
+                        const int col = sl + jx;
+                        if (jx < J && col >= x_lo && col < x_hi) {
+                            const float wt = wo * wx[k];
+                            float2* t = arow + col * CPT;
+                            float2 v = *t;
+                            v.x = fmaf(wt, yv.x, v.x);
+                            v.y = fmaf(wt, yv.y, v.y);
+                            *t = v;
                         }
-                        __syncwarp();   // the next point's cells may be another lane's
+                    }
+                    __syncwarp();   // the next point's cells may be another lane's
+                }
+            }
+        } else {
+            for (int u = warp; u < R * nseg; u += NW) {
+                const int r = u / nseg, sg = u - r * nseg;
+                const int x_lo = sg * segw, x_hi = min(Bl, x_lo + segw);
+                int l0 = r, l1 = 0;
+                if (D == 3) {
+                    l0 = r / Bt[1];
+                    l1 = r - l0 * Bt[1];
+                }
+                float2* arow = s_acc + (size_t)r * Bl * CPT + c;
+#pragma unroll 1
+                for (int a0 = 0; a0 < J; ++a0) {
+#pragma unroll 1
+                    for (int a1 = 0; a1 < (D > 2 ? J : 1); ++a1) {
+                        const int b = D == 2 ? l0 + a0 : (l0 + a0) * E[1] + (l1 + a1);
+                        const int h1 = s_off[b + 1];
+                        for (int hh = s_off[b]; hh < h1; ++hh) {
+                            const int h = s_list[hh];
+                            const float* w = s_w + h * WP;
+                            float wo = w[J - 1 - a0];
+                            if (D > 2) wo *= w[J + J - 1 - a1];
+                            const float2 yv = s_y[(size_t)h * YP + c];
+                            const int sl = s_el[h];
+#pragma unroll
+                            for (int k = 0; k < NJX; ++k) {
+                                const int jx = jg + k * JPL;
+                                const int col = sl + jx;
+                                if (jx < J && col >= x_lo && col < x_hi) {
+                                    const float wt = wo * w[(D - 1) * J + jx];
+                                    float2* t = arow + col * CPT;
+                                    float2 v = *t;
+                                    v.x = fmaf(wt, yv.x, v.x);
+                                    v.y = fmaf(wt, yv.y, v.y);
+                                    *t = v;
+                                }
+                            }
+                            __syncwarp();   // the next point's cells may be another lane's
+                        }
                     }
                 }
             }
         }
-    }
-    __syncthreads();   // every warp's rows are complete
+        __syncthreads();   // every warp's rows are complete
 
-    // write the tile coil-fastest: a tile row is Bt_last cells, contiguous in the grid
-    const int K1 = D > 1 ? Kd[1] : 1, K2 = D > 2 ? Kd[2] : 1;
-    if (D == 2 && nparts == 1 && ncc == CPT && a.C == CPT) {
-        // all coils in this block: each tile row is one contiguous run of Bl * CPT complex
-        const int per_row4 = Bl * CPT / 2;
-        for (int row = warp; row < R; row += NW) {
-            const float4* src = (const float4*)(s_acc + (size_t)row * Bl * CPT);
-            float4* dst = (float4*)(a.grid + ((int64_t)(org[0] + row) * K1 + org[1]) * CPT);
-            for (int i = lane; i < per_row4; i += 32) dst[i] = src[i];
+        // write the tile coil-fastest: a tile row is Bt_last cells, contiguous in the grid
+        const int K1 = D > 1 ? Kd[1] : 1, K2 = D > 2 ? Kd[2] : 1;
+        if (D == 2 && nparts == 1 && ncc == CPT && a.C == CPT) {
+            // all coils in this block: each tile row is one contiguous run of Bl * CPT complex
+            const int per_row4 = Bl * CPT / 2;
+            for (int row = warp; row < R; row += NW) {
+                const float4* src = (const float4*)(s_acc + (size_t)row * Bl * CPT);
+                float4* dst = (float4*)(a.grid + ((int64_t)(org[0] + row) * K1 + org[1]) * CPT);
+                for (int i = lane; i < per_row4; i += 32) dst[i] = src[i];
+            }
+        } else {
+            const int rowlen = Bl * ncc;
+            const uint32_t mg = ncc > 1 ? (uint32_t)((((uint64_t)1 << 32) + ncc - 1) / ncc) : 0u;
+            for (int f = tid; f < R * rowlen; f += nt) {
+                const int row = f / rowlen, i = f - row * rowlen;
+                const int cr = (int)div_magic((uint32_t)i, (uint32_t)ncc, mg);
+                const int cc = i - cr * ncc;
+                int r0 = row, r1 = 0;
+                if (D == 3) { r1 = row % Bt[1]; r0 = row / Bt[1]; }
+                const int64_t gcell = D == 2 ? (int64_t)(org[0] + r0) * K1 + org[1] + cr
+                                             : ((int64_t)(org[0] + r0) * K1 + (org[1] + r1)) * K2 + org[2] + cr;
+                const float2 v = s_acc[(size_t)(row * Bl + cr) * CPT + cc];
+                float2* dst = a.grid + gcell * a.C + c0 + cc;
+                if (nparts == 1) *dst = v;
+                else if (v.x != 0.f || v.y != 0.f) atomicAdd(dst, v);
+            }
         }
-        return;
+        if (itn >= nitems) break;
+        it = itn;
+        item = itemn;
+        __syncthreads();   // the shared tile and lists are reused by the next item
     }
-    const int rowlen = Bl * ncc;
-    const uint32_t mg = ncc > 1 ? (uint32_t)((((uint64_t)1 << 32) + ncc - 1) / ncc) : 0u;
-    for (int f = tid; f < R * rowlen; f += nt) {
-        const int row = f / rowlen, i = f - row * rowlen;
-        const int cr = (int)div_magic((uint32_t)i, (uint32_t)ncc, mg);
-        const int cc = i - cr * ncc;
-        int r0 = row, r1 = 0;
-        if (D == 3) { r1 = row % Bt[1]; r0 = row / Bt[1]; }
-        const int64_t gcell = D == 2 ? (int64_t)(org[0] + r0) * K1 + org[1] + cr
-                                     : ((int64_t)(org[0] + r0) * K1 + (org[1] + r1)) * K2 + org[2] + cr;
-        const float2 v = s_acc[(size_t)(row * Bl + cr) * CPT + cc];
-        float2* dst = a.grid + gcell * a.C + c0 + cc;
-        if (nparts == 1) *dst = v;
-        else if (v.x != 0.f || v.y != 0.f) atomicAdd(dst, v);
+}
+
+// Streaming multiprocessors of the current device (queried once per device).
+static int device_sms() {
+    static std::atomic<int> n[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    int v = n[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+        n[dev].store(v, std::memory_order_relaxed);
     }
+    return v;
 }
 
 template <int D, int J>
@@ -777,7 +814,8 @@ static cudaError_t spread_rows_cpt(const SpreadArgs& a, cudaStream_t s, int thre
     const size_t smem = (size_t)tcells * cpt * sizeof(float2) + (size_t)a.P * (cpt + 1) * sizeof(float2) +
                         (size_t)a.P * WP * sizeof(float) + 3 * (size_t)a.P * sizeof(int) +
                         (size_t)(2 * NB + 1) * sizeof(int);
-    dim3 grid((unsigned)a.max_items, (unsigned)((a.C + cpt - 1) / cpt));
+    // persistent: two blocks per SM (the shared tile and lists take ~84 KB) walk the items
+    dim3 grid((unsigned)std::min<int64_t>(a.max_items, 2 * (int64_t)device_sms()), (unsigned)((a.C + cpt - 1) / cpt));
     if (cpt == 4) {
         ensure_smem<k_spread_rows<D, J, 4>>(smem);
         k_spread_rows<D, J, 4><<<grid, threads, smem, s>>>(a);
