@@ -48,40 +48,62 @@ cudaError_t launch_bin_scatter(const SortArgs& a, cudaStream_t s);   // records 
 // Bins whose points can reach tile `bin` (tiles are the bins).  A window
 // covers J cells to the right of its start, so along each axis these are the
 // tile's own bin and the bins holding the J-1 cells before its first cell
-// (periodic; at most three, without repeats).  Returns their linear ids.
-__device__ __forceinline__ int neighbour_bins(int D, const int* nb, const int* B, const int* K, int J, int bin,
-                                              int* out) {
-    int bc[kMaxDim] = {0, 0, 0};
+// (periodic; at most three, without repeats).  Writes the tile's list entry,
+// tn[0] = count, then (first point, candidate prefix) pairs and the total, and
+// returns the candidate count.  Every array index is fixed after unrolling, so
+// nothing goes to local memory.
+__device__ __forceinline__ int tile_bin_list(int D, const int* nb, const int* B, const int* K, int J, int bin,
+                                             const int* offsets, int* tn) {
+    int x[kMaxDim][3], n[kMaxDim];
     int r = bin;
-    for (int d = D - 1; d >= 0; --d) {
-        bc[d] = r % nb[d];
-        r /= nb[d];
-    }
-    int lists[kMaxDim][3], len[kMaxDim] = {1, 1, 1};
-    for (int d = 0; d < kMaxDim; ++d) lists[d][0] = 0;
-    for (int d = 0; d < D; ++d) {
-        const int org = bc[d] * B[d];
-        int c1 = org - 1, c2 = org - (J - 1);
-        if (c1 < 0) c1 += K[d];
-        if (c2 < 0) c2 += K[d];
-        const int cand[3] = {bc[d], c1 / B[d], c2 / B[d]};
-        len[d] = 0;
-        for (int o = 0; o < 3; ++o) {
-            bool seen = false;
-            for (int q = 0; q < len[d]; ++q) seen |= lists[d][q] == cand[o];
-            if (!seen) lists[d][len[d]++] = cand[o];
+#pragma unroll
+    for (int d = kMaxDim - 1; d >= 0; --d) {
+        x[d][0] = x[d][1] = x[d][2] = 0;
+        n[d] = 1;
+        if (d < D) {
+            const int bc = r % nb[d];
+            r /= nb[d];
+            const int org = bc * B[d];
+            int c1 = org - 1, c2 = org - (J - 1);
+            if (c1 < 0) c1 += K[d];
+            if (c2 < 0) c2 += K[d];
+            const int b1 = c1 / B[d], b2 = c2 / B[d];
+            x[d][0] = bc;   // own bin, then those of cells org-1 and org-(J-1), in order, no repeats
+            if (b1 != bc) {
+                x[d][1] = b1;
+                n[d] = 2;
+                if (b2 != bc && b2 != b1) {
+                    x[d][2] = b2;
+                    n[d] = 3;
+                }
+            } else if (b2 != bc) {
+                x[d][1] = b2;
+                n[d] = 2;
+            }
         }
     }
-    int n = 0;
-    for (int i0 = 0; i0 < len[0]; ++i0)
-        for (int i1 = 0; i1 < len[1]; ++i1)
-            for (int i2 = 0; i2 < len[2]; ++i2) {
-                int id = lists[0][i0];
-                if (D > 1) id = id * nb[1] + lists[1][i1];
-                if (D > 2) id = id * nb[2] + lists[2][i2];
-                out[n++] = id;
+    int q = 0, cand = 0;
+#pragma unroll
+    for (int i0 = 0; i0 < 3; ++i0)
+#pragma unroll
+        for (int i1 = 0; i1 < 3; ++i1)
+#pragma unroll
+            for (int i2 = 0; i2 < 3; ++i2) {
+                if (i0 < n[0] && i1 < n[1] && i2 < n[2]) {
+                    int id = x[0][i0];
+                    if (D > 1) id = id * nb[1] + x[1][i1];
+                    if (D > 2) id = id * nb[2] + x[2][i2];
+                    const int st = offsets[id];
+                    tn[1 + 2 * q] = st;
+                    tn[2 + 2 * q] = cand;
+                    cand += offsets[id + 1] - st;
+                    ++q;
+                }
             }
-    return n;
+    tn[0] = q;
+    tn[1 + 2 * q] = 0;
+    tn[2 + 2 * q] = cand;
+    return cand;
 }
 
 // -------------------------------------------------------------------- FFT

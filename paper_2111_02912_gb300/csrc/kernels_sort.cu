@@ -144,19 +144,7 @@ __global__ void __launch_bounds__(1024) k_bin_scan(SortArgs a) {
 __global__ void k_tile_lists(SortArgs a) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= a.nbins) return;
-    int nbr[27];
-    const int nn = neighbour_bins(a.D, a.nb, a.B, a.K, a.J, b, nbr);
-    int* tn = a.tile_nbr + (int64_t)b * kNbrStride;
-    tn[0] = nn;
-    int cand = 0;
-    for (int q = 0; q < nn; ++q) {
-        const int st = a.offsets[nbr[q]];
-        tn[1 + 2 * q] = st;
-        tn[2 + 2 * q] = cand;
-        cand += a.offsets[nbr[q] + 1] - st;
-    }
-    tn[1 + 2 * nn] = 0;
-    tn[2 + 2 * nn] = cand;
+    const int cand = tile_bin_list(a.D, a.nb, a.B, a.K, a.J, b, a.offsets, a.tile_nbr + (int64_t)b * kNbrStride);
     a.tile_parts[b] = max(1, (cand + a.P - 1) / a.P);
 }
 
@@ -207,20 +195,8 @@ __global__ void __launch_bounds__(1024) k_sort_tables(SortArgs a) {
     }
     __syncthreads();   // offsets are read by other threads below (global, same block)
     int parts_sum = 0;
-    int nbr[27];
     for (int b = lo; b < hi; ++b) {
-        const int nn = neighbour_bins(a.D, a.nb, a.B, a.K, a.J, b, nbr);
-        int* tn = a.tile_nbr + (int64_t)b * kNbrStride;
-        tn[0] = nn;
-        int cand = 0;
-        for (int q = 0; q < nn; ++q) {
-            const int st = a.offsets[nbr[q]];
-            tn[1 + 2 * q] = st;
-            tn[2 + 2 * q] = cand;
-            cand += a.offsets[nbr[q] + 1] - st;
-        }
-        tn[1 + 2 * nn] = 0;
-        tn[2 + 2 * nn] = cand;
+        const int cand = tile_bin_list(a.D, a.nb, a.B, a.K, a.J, b, a.offsets, a.tile_nbr + (int64_t)b * kNbrStride);
         const int parts = max(1, (cand + a.P - 1) / a.P);
         a.tile_parts[b] = parts;
         parts_sum += parts;
