@@ -292,15 +292,16 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
     const int P = a.P;
     const int c0 = blockIdx.y * CPT;
     const int ncc = min(CPT, a.C - c0);
-    // shared layout: weights [P][D*J], y [P][CPT+1], last start coordinate, row and original index
-    // per hit [P] each, sorted hits [P], row cursors [NR+1]
+    // shared layout: weights [P][D*J], y [P][CPT+1], last start coordinate and original index
+    // per hit [P] each, sorted hits [P], row starts/ends [NR+1], cursors [NR], arrival list [P]
     float* s_w = (float*)smem4;
     float2* s_y = (float2*)(s_w + P * D * J + ((P * D * J) & 1));
     int* s_el = (int*)(s_y + (size_t)P * (CPT + 1));
-    int* s_row = s_el + P;
-    int* s_orig = s_row + P;
+    int* s_orig = s_el + P;
     int* s_list = s_orig + P;
-    int* s_cnt = s_list + P;
+    int* s_cnt = s_list + P;   // [NR + 1]
+    int* s_cur = s_cnt + NR + 1;   // [NR]
+    int* s_tmp = s_cur + NR;   // [P] hits in arrival order within their rows
 
     {
         const int* tn = a.tile_nbr + (int64_t)tile * kNbrStride;
@@ -336,7 +337,6 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
             my_row = D == 2 ? e[0] : e[0] * E[1] + e[1];
             my_orig = ix.w;
             s_el[my_slot] = e[D - 1];
-            s_row[my_slot] = my_row;
             s_orig[my_slot] = my_orig;
             const float* pw = a.pts.w + p * a.pts.ws;
             float* w = s_w + my_slot * (D * J);
@@ -353,40 +353,56 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
         }
     }
     __syncthreads();
-    // exclusive scan of the row counts: each thread a chunk, then a block scan of the chunk sums
+    // exclusive scan of the row counts: each thread a chunk, then a two-level shuffle scan of
+    // the chunk sums; s_cnt[r] = first slot of row r, s_cur[r] a copy used as placement cursor
     {
-        __shared__ int s_part[512];
+        __shared__ int s_wsum[32];
+        const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
         const int per = (NR + nt - 1) / nt;
         const int b0 = min(NR, tid * per), b1 = min(NR, b0 + per);
         int sum = 0;
         for (int b = b0; b < b1; ++b) sum += s_cnt[b];
-        s_part[tid] = sum;
-        __syncthreads();
-        for (int off = 1; off < nt; off <<= 1) {
-            const int v = tid >= off ? s_part[tid - off] : 0;
-            __syncthreads();
-            s_part[tid] += v;
-            __syncthreads();
+        int x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        int run = tid ? s_part[tid - 1] : 0;
+        if (lane == 31) s_wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int w = lane < nw ? s_wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < nw) s_wsum[lane] = w;
+        }
+        __syncthreads();
+        int run = x - sum + (wid ? s_wsum[wid - 1] : 0);
         for (int b = b0; b < b1; ++b) {
             const int c = s_cnt[b];
             s_cnt[b] = run;
+            s_cur[b] = run;
             run += c;
         }
         if (tid == nt - 1) s_cnt[NR] = run;
     }
     __syncthreads();
-    // place hits in a fixed order: within a row by original point index, so the sums below
-    // do not depend on the order in which threads arrived.  s_cnt[r] then marks the end of row r.
+    // place hits in a fixed order: first in arrival order inside their row's range, then each
+    // hit ranks itself by original point index among its own row's hits (rows hold few), so
+    // the sums below do not depend on the order in which threads arrived.
+    if (my_slot >= 0) s_tmp[atomicAdd(&s_cur[my_row], 1)] = my_slot;
+    __syncthreads();
     if (my_slot >= 0) {
-        const int nh = s_nh;
+        const int r0 = s_cnt[my_row], r1 = s_cur[my_row];
         int rank = 0;
-        for (int h = 0; h < nh; ++h) rank += s_row[h] == my_row && s_orig[h] < my_orig;
-        s_list[s_cnt[my_row] + rank] = my_slot;
+        for (int k = r0; k < r1; ++k) rank += s_orig[s_tmp[k]] < my_orig;
+        s_list[r0 + rank] = my_slot;
     }
     __syncthreads();
-    if (my_slot >= 0) atomicAdd(&s_cnt[my_row], 1);   // start -> end of the row (order-free)
+    for (int i = tid; i < NR; i += nt) s_cnt[i] = s_cur[i];   // s_cnt[r] now marks the end of row r
     __syncthreads();
 
     // gather: thread t owns cell t (one thread per tile cell).  The points covering cell l
@@ -464,7 +480,7 @@ static cudaError_t spread_cells_cpt(const SpreadArgs& a, cudaStream_t s, int thr
     int E = 1;   // row bins
     for (int d = 0; d < D - 1; ++d) E *= a.B[d] + J - 1;
     const size_t smem = (size_t)a.P * D * J * sizeof(float) + sizeof(float) + (size_t)a.P * (cpt + 1) * sizeof(float2) +
-                        4 * (size_t)a.P * sizeof(int) + (size_t)(E + 1) * sizeof(int);
+                        4 * (size_t)a.P * sizeof(int) + (size_t)(2 * E + 1) * sizeof(int);
     dim3 grid((unsigned)a.max_items, (unsigned)((a.C + cpt - 1) / cpt));
     if (cpt <= 4) {
         ensure_smem<k_spread_cells<D, J, 4>>(smem);
