@@ -287,8 +287,11 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
             E[d] = Bt[d] + J - 1;
         }
     }
-    // row bins: all start coordinates but the last (E0 in 2-D, E0 * E1 in 3-D)
+    // row bins: all start coordinates but the last (E0 in 2-D, E0 * E1 in 3-D); hits are
+    // bucketed by their full window-start cell, key = row * El + e_last
     const int NR = D == 2 ? E[0] : E[0] * E[1];
+    const int El = E[D - 1];
+    const int NK = NR * El;
     const int P = a.P;
     const int c0 = blockIdx.y * CPT;
     const int ncc = min(CPT, a.C - c0);
@@ -299,9 +302,9 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
     int* s_el = (int*)(s_y + (size_t)P * (CPT + 1));
     int* s_orig = s_el + P;
     int* s_list = s_orig + P;
-    int* s_cnt = s_list + P;   // [NR + 1]
-    int* s_cur = s_cnt + NR + 1;   // [NR]
-    int* s_tmp = s_cur + NR;   // [P] hits in arrival order within their rows
+    int* s_cnt = s_list + P;       // [NK + 1] first slot of each start cell
+    int* s_cur = s_cnt + NK + 1;   // [NK]
+    int* s_tmp = s_cur + NK;       // [P] hits in arrival order within their start cells
 
     {
         const int* tn = a.tile_nbr + (int64_t)tile * kNbrStride;
@@ -309,7 +312,7 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
         if (tid < 27) s_start[tid] = tn[1 + 2 * tid];      // entries past the count are never used
         if (tid < 28) s_pref[tid] = tn[2 + 2 * tid];
     }
-    for (int i = tid; i <= NR; i += nt) s_cnt[i] = 0;
+    for (int i = tid; i <= NK; i += nt) s_cnt[i] = 0;
     __syncthreads();
 
     // stage: thread t takes candidate lo + t
@@ -334,7 +337,7 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
         }
         if (hit) {
             my_slot = atomicAdd(&s_nh, 1);
-            my_row = D == 2 ? e[0] : e[0] * E[1] + e[1];
+            my_row = (D == 2 ? e[0] : e[0] * E[1] + e[1]) * El + e[D - 1];   // start-cell key
             my_orig = ix.w;
             s_el[my_slot] = e[D - 1];
             s_orig[my_slot] = my_orig;
@@ -358,8 +361,8 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
     {
         __shared__ int s_wsum[32];
         const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-        const int per = (NR + nt - 1) / nt;
-        const int b0 = min(NR, tid * per), b1 = min(NR, b0 + per);
+        const int per = (NK + nt - 1) / nt;
+        const int b0 = min(NK, tid * per), b1 = min(NK, b0 + per);
         int sum = 0;
         for (int b = b0; b < b1; ++b) sum += s_cnt[b];
         int x = sum;
@@ -387,12 +390,12 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
             s_cur[b] = run;
             run += c;
         }
-        if (tid == nt - 1) s_cnt[NR] = run;
+        if (tid == nt - 1) s_cnt[NK] = run;
     }
     __syncthreads();
-    // place hits in a fixed order: first in arrival order inside their row's range, then each
-    // hit ranks itself by original point index among its own row's hits (rows hold few), so
-    // the sums below do not depend on the order in which threads arrived.
+    // place hits in a fixed order: first in arrival order inside their start cell's range, then
+    // each hit ranks itself by original point index among the hits of its own start cell (few),
+    // so the sums below do not depend on the order in which threads arrived.
     if (my_slot >= 0) s_tmp[atomicAdd(&s_cur[my_row], 1)] = my_slot;
     __syncthreads();
     if (my_slot >= 0) {
@@ -401,8 +404,6 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
         for (int k = r0; k < r1; ++k) rank += s_orig[s_tmp[k]] < my_orig;
         s_list[r0 + rank] = my_slot;
     }
-    __syncthreads();
-    for (int i = tid; i < NR; i += nt) s_cnt[i] = s_cur[i];   // s_cnt[r] now marks the end of row r
     __syncthreads();
 
     // gather: thread t owns cell t (one thread per tile cell).  The points covering cell l
@@ -428,11 +429,11 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
 #pragma unroll 1
             for (int a1 = 0; a1 < (D > 2 ? J : 1); ++a1) {
                 const int row = D == 2 ? l[0] + a0 : (l[0] + a0) * E[1] + (l[1] + a1);
-                const int h0 = row ? s_cnt[row - 1] : 0, h1 = s_cnt[row];   // cursors now mark row ends
+                // start cells (row, ll .. ll + J - 1): one contiguous range of the sorted hits
+                const int h0 = s_cnt[row * El + ll], h1 = s_cnt[row * El + ll + J];
                 for (int hh = h0; hh < h1; ++hh) {
                     const int h = s_list[hh];
                     const int al = s_el[h] - ll;
-                    if (al < 0 || al >= J) continue;
                     const float* w = s_w + h * (D * J);
                     float wt = w[J - 1 - a0] * w[(D - 1) * J + J - 1 - al];
                     if (D > 2) wt *= w[J + J - 1 - a1];
@@ -477,8 +478,8 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
 template <int D, int J>
 static cudaError_t spread_cells_cpt(const SpreadArgs& a, cudaStream_t s, int threads) {
     const int cpt = a.CC;
-    int E = 1;   // row bins
-    for (int d = 0; d < D - 1; ++d) E *= a.B[d] + J - 1;
+    int E = 1;   // start-cell buckets
+    for (int d = 0; d < D; ++d) E *= a.B[d] + J - 1;
     const size_t smem = (size_t)a.P * D * J * sizeof(float) + sizeof(float) + (size_t)a.P * (cpt + 1) * sizeof(float2) +
                         4 * (size_t)a.P * sizeof(int) + (size_t)(2 * E + 1) * sizeof(int);
     dim3 grid((unsigned)a.max_items, (unsigned)((a.C + cpt - 1) / cpt));
