@@ -45,6 +45,9 @@ CASES = [
     ("2d_fft2_low_accuracy", (64, 64), 1500, 2, True, dict(J=5, sigma=1.25)),   # K = 80
     ("3d_fft2_maps", (32, 40, 48), 2000, 2, True, {}),
     ("1d_fft2", (256,), 900, 3, True, {}),
+    # two-phase sizes K = 768 (24 x 32) and 384 (16 x 24)
+    ("2d_fft2_split_768", (384, 64), 1500, 2, True, {}),
+    ("2d_fft2_split_384", (192, 40), 1200, 3, False, {}),
 ]
 
 
