@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sigma", type=float, default=2.0, help="grid oversampling (radial320 workload)")
     ap.add_argument("--J", type=int, default=6, help="interpolation width (radial320 workload)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="radial320: time the eager per-call step only (default: replay the step from a CUDA graph)")
     return ap.parse_args()
 
 
@@ -194,13 +196,15 @@ def run_ours(args):
     om, X, S, V = t(w["omega"]), t(w["x"]), t(w["smaps"]), t(w["v"])
     plan = Plan(w["shape"], om, max_coils=C, J=args.J, sigma=args.sigma)
     y = torch.empty((C, M), dtype=torch.complex64, device=dev)
+    go = torch.empty((D, M), dtype=torch.float32, device=dev)
+    gx = torch.empty(tuple(w["shape"]), dtype=torch.complex64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
     def step():
         plan.set_points(om)
         plan.forward(X, S, out=y)
-        return plan.vjp_omega_x(X, V, S)
+        return plan.vjp_omega_x(X, V, S, out=(go, gx))
 
     def barrier():
         if ws > 1:
@@ -210,7 +214,28 @@ def run_ours(args):
     for _ in range(max(3, args.warmup)):
         step()
 
-    def timed_region(profile):
+    # The whole step (sort, forward, VJP: the same kernels, inputs read at replay) captured once in a
+    # CUDA graph and replayed each step, as a static-shape training loop would; the eager per-call
+    # step is timed as well.
+    graph, graph_launches = None, 0
+    if not args.no_graph:
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                step()
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        c0 = nufft_launch_count()
+        with torch.cuda.graph(graph):
+            step()
+        graph_launches = nufft_launch_count() - c0
+        torch.cuda.synchronize()
+        for _ in range(max(3, args.warmup)):
+            graph.replay()
+
+    def timed_region(profile, use_graph=False):
         plan.profile_enable(profile)
         if profile:
             plan.profile_read()
@@ -221,19 +246,24 @@ def run_ours(args):
         for a, b in evs:
             flush.fill_(1.0)                 # evict L2 between steps (outside the events)
             a.record(stream)
-            step()
+            if use_graph:
+                graph.replay()
+            else:
+                step()
             b.record(stream)
         barrier()
-        n1 = nufft_launch_count()
+        n1 = nufft_launch_count() + (graph_launches * len(evs) if use_graph else 0)
         ms = [a.elapsed_time(b) for a, b in evs]
         prof = plan.profile_read() if profile else None
         plan.profile_enable(False)
         return ms, n1 - n0, prof
 
     with ClockSampler(local) as clk:
-        ms, launches, _ = timed_region(False)
+        ms, launches, _ = timed_region(False, use_graph=graph is not None)
+        ms_eager, _, _ = timed_region(False) if graph is not None else (ms, 0, None)
     clocks = clk.summary()
     total_ms = max_over_ranks(float(sum(ms)), dev)
+    eager_ms = max_over_ranks(float(sum(ms_eager)), dev)
     value = ws * units * args.steps / (total_ms / 1e3)
 
     # kernel roofline: the same timed region with per-kernel events on the launching stream
@@ -301,7 +331,10 @@ def run_ours(args):
             "data": "synthetic (seeded; shapes of the paper's 2-D multicoil radial case)",
             "config": {"workload": WORKLOAD, "points": M, "coils": C, "channels_per_step": C * (1 + D),
                        "units_per_step": units, "l2": "flushed between timed steps (256 MiB write)",
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "step_replay": "CUDA graph of the whole step, captured once" if graph is not None
+                       else "eager per-call",
+                       "eager_ms_per_step": eager_ms / args.steps},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)

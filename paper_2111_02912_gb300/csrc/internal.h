@@ -176,6 +176,7 @@ struct GatherArgs {
     const float* domega;  // [D][M]
     const float2* v;      // [C][M]
     float* grad;          // [D][M]
+    float2* v_sorted;     // VJP: if set, v is also written here in sorted point order, [C][M]
 };
 cudaError_t launch_gather_d1(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);
 cudaError_t launch_gather_d2(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);

@@ -168,7 +168,9 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
             if (!ok[k]) continue;
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                const float2 v = __ldg(a.v + (int64_t)(W * (lane_g + k * G) + i) * M + orig);
+                const int64_t cv = W * (lane_g + k * G) + i;
+                const float2 v = __ldg(a.v + cv * M + orig);
+                if (a.v_sorted) a.v_sorted[cv * M + pt] = v;   // for the adjoint spread of the same v
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
                     const float2 g = acc[d][k][i];

@@ -496,7 +496,9 @@ int forward_grids(nufft_plan_s* p, int C, int nd, int has_plain, const float2* x
 }
 
 // Adjoint of the interpolation + FFT + scaling for C coil channels of y.
-int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, float2* xout, cudaStream_t s) {
+// ysorted: y already copied into T in sorted point order (by the VJP gather), else null.
+int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, float2* xout, cudaStream_t s,
+                 const float2* ysorted = nullptr) {
     const int D = p->D;
     int st;
     // spread: output-driven tiles; only tiles split over several work items are cleared first
@@ -534,7 +536,10 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
         sa.CC = C <= 4 ? 4 : (C <= 8 ? 8 : 16);
         // y in sorted point order (in T, free until the inverse FFT passes): the tile kernels then
         // read it coalesced and without waiting for the point record
-        if ((size_t)C * (size_t)p->M <= p->T_elems && p->M > 0) {
+        if (ysorted) {
+            sa.y = ysorted;
+            sa.y_sorted = 1;
+        } else if ((size_t)C * (size_t)p->M <= p->T_elems && p->M > 0) {
             if ((st = launch(p, PK_PERMUTE_Y, s,
                              [&] { return launch_permute_y(p->d_pidx, y, p->d_T, p->M, C, s); })))
                 return st;
@@ -760,15 +765,22 @@ int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_
     if ((p->M > 0 && !v) || (grad_omega && !x)) return fail(NUFFT_ERR_INVALID_ARG, "x or v is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
+    // With both outputs the gather also writes v in sorted point order into T (free once the
+    // last forward pass has read it) for the adjoint's spread, which then needs no reorder pass.
+    const float2* vsorted = nullptr;
     if (grad_omega && p->M > 0) {
         if ((st = forward_grids(p, C, p->D, 0, (const float2*)x, (const float2*)smaps, s))) return st;
         GatherArgs g = gather_args(p, C, p->D, 0);
         g.v = (const float2*)v;
         g.grad = grad_omega;
+        if (grad_x && p->cell_spread && (size_t)C * (size_t)p->M <= p->T_elems) {
+            g.v_sorted = p->d_T;
+            vsorted = p->d_T;
+        }
         const int cpl = gather_cpl(g);
         if ((st = launch(p, PK_GATHER_VJP, s, [&] { return launch_gather(GM_VJP, g, cpl, s); }))) return st;
     }
-    if (grad_x) return adjoint_impl(p, C, (const float2*)v, (const float2*)smaps, (float2*)grad_x, s);
+    if (grad_x) return adjoint_impl(p, C, (const float2*)v, (const float2*)smaps, (float2*)grad_x, s, vsorted);
     return NUFFT_OK;
 }
 
