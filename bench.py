@@ -295,15 +295,36 @@ def run_ours(args):
     h2d = sum(a.numel() * a.element_size() for a in (hx, hs, hom, hv))
     d2h = sum(a.numel() * a.element_size() for a in (hy, hgo, hgx))
 
+    # Copies run on a second stream and each input is waited for just before its first use:
+    # omega (the sort), then x and the maps (forward), then v (VJP) arrives during the forward;
+    # y goes back to the host while the VJP runs.  The step's events bracket both streams.
+    copy_stream = torch.cuda.Stream()
+    ev_om, ev_xs, ev_v, ev_y, ev_done = (torch.cuda.Event() for _ in range(5))
+
     def e2e_step():
-        om.copy_(hom, non_blocking=True)
-        X.copy_(hx, non_blocking=True)
-        S.copy_(hs, non_blocking=True)
-        V.copy_(hv, non_blocking=True)
-        go, gx = step()
-        hy.copy_(y, non_blocking=True)
-        hgo.copy_(go, non_blocking=True)
-        hgx.copy_(gx, non_blocking=True)
+        copy_stream.wait_stream(stream)          # the previous step no longer reads the buffers
+        with torch.cuda.stream(copy_stream):
+            om.copy_(hom, non_blocking=True)
+            ev_om.record(copy_stream)
+            X.copy_(hx, non_blocking=True)
+            S.copy_(hs, non_blocking=True)
+            ev_xs.record(copy_stream)
+            V.copy_(hv, non_blocking=True)
+            ev_v.record(copy_stream)
+        stream.wait_event(ev_om)
+        plan.set_points(om)
+        stream.wait_event(ev_xs)
+        plan.forward(X, S, out=y)
+        ev_y.record(stream)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(ev_y)
+            hy.copy_(y, non_blocking=True)
+            ev_done.record(copy_stream)
+        stream.wait_event(ev_v)
+        go_, gx_ = plan.vjp_omega_x(X, V, S, out=(go, gx))
+        hgo.copy_(go_, non_blocking=True)
+        hgx.copy_(gx_, non_blocking=True)
+        stream.wait_event(ev_done)
 
     for _ in range(3):
         e2e_step()
@@ -317,7 +338,9 @@ def run_ours(args):
     barrier()
     e2e_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in evs)), dev)
     e2e = {"value": ws * units * args.steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps,
+           "path": "public API calls (eager), copies from pinned host memory on a second stream overlapped "
+                   "with the compute that does not need them"}
 
     if rank != 0:
         if ws > 1:
