@@ -17,6 +17,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -131,11 +132,12 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # samples go to a private temporary file (NUFFT_BENCH_CLOCKS names a file to keep them in)
+        self.path = os.environ.get("NUFFT_BENCH_CLOCKS") or os.path.join(
+            tempfile.gettempdir(), "nufft_bench_clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
