@@ -95,6 +95,16 @@ struct nufft_plan_s {
     int* d_keyid = nullptr;
     int4* d_pidx = nullptr;
     float4* d_pfrac = nullptr;
+    float* d_om = nullptr;   // [D][M_cap] copy of omega taken by set_points
+    // The sort runs at the first call after set_points that needs the points, on a stream of the
+    // plan, beside that call's FFT passes (which do not need them); the call joins it before its
+    // first kernel that reads the sorted points.  Fork and join stay inside one call.
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    bool sort_pending = false;   // eager: omega copied by set_points, not yet sorted
+    bool join_pending = false;   // sort launched on aux, not yet joined into a stream
+    bool cap_pending = false;    // the same for a set_points recorded into capture cap_id
+    unsigned long long cap_id = 0;
     float* d_pw = nullptr;   // [M_cap][ws] kernel weights of the sorted points
     int ws = 4;              // D*J rounded up to a multiple of 4
     float c_hi[3] = {0, 0, 0}, c_lo[3] = {0, 0, 0};
@@ -179,8 +189,11 @@ void free_plan(nufft_plan_s* p) {
     for (int d = 0; d < 3; ++d) { cudaFree(p->d_deap[d]); cudaFree(p->d_tw[d]); }
     cudaFree(p->d_kcount); cudaFree(p->d_offsets); cudaFree(p->d_item_off); cudaFree(p->d_tile_parts); cudaFree(p->d_heavy); cudaFree(p->d_tile_nbr);
     cudaFree(p->d_nitems); cudaFree(p->d_items); cudaFree(p->d_local); cudaFree(p->d_keyid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
-    cudaFree(p->d_pw);
+    cudaFree(p->d_pw); cudaFree(p->d_om);
     cudaFree(p->d_G); cudaFree(p->d_T);
+    if (p->aux) cudaStreamDestroy(p->aux);
+    if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+    if (p->join_ev) cudaEventDestroy(p->join_ev);
     for (auto& e : p->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto e : p->pool) cudaEventDestroy(e);
     delete p;
@@ -288,23 +301,25 @@ size_t max_items(const nufft_plan_s& p, int64_t cap) {
 }
 
 size_t point_bytes(const nufft_plan_s& p, int64_t cap) {
-    size_t b = (size_t)cap * (2 * sizeof(int) + sizeof(int4) + sizeof(float4) + p.ws * sizeof(float)) +
+    size_t b = (size_t)cap * (2 * sizeof(int) + sizeof(int4) + sizeof(float4) + (p.ws + p.D) * sizeof(float)) +
                max_items(p, cap) * sizeof(int4);
     return b;
 }
 
 int alloc_points(nufft_plan_s* p, int64_t cap) {
     cudaFree(p->d_items); cudaFree(p->d_local); cudaFree(p->d_keyid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
-    cudaFree(p->d_pw);
+    cudaFree(p->d_pw); cudaFree(p->d_om);
     p->d_items = nullptr; p->d_local = p->d_keyid = nullptr; p->d_pidx = nullptr; p->d_pfrac = nullptr;
     p->d_pw = nullptr;
+    p->d_om = nullptr;
     const size_t c = (size_t)std::max<int64_t>(cap, 1);
     if (cudaMalloc(&p->d_items, max_items(*p, cap) * sizeof(int4)) != cudaSuccess ||
         cudaMalloc(&p->d_local, c * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&p->d_keyid, c * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&p->d_pidx, c * sizeof(int4)) != cudaSuccess ||
         cudaMalloc(&p->d_pfrac, c * sizeof(float4)) != cudaSuccess ||
-        cudaMalloc(&p->d_pw, c * p->ws * sizeof(float)) != cudaSuccess) {
+        cudaMalloc(&p->d_pw, c * p->ws * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&p->d_om, c * p->D * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         return fail(NUFFT_ERR_OOM, "device allocation of point arrays failed");
     }
@@ -345,35 +360,95 @@ SortArgs sort_args(nufft_plan_s* p, const float* omega) {
     return a;
 }
 
+int sort_rest(nufft_plan_s* p, cudaStream_t s);
+
+// True, with the capture sequence id, when s is recording into a CUDA graph.
+bool capture_id(cudaStream_t s, unsigned long long& id) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamGetCaptureInfo(s, &cs, &id) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusActive;
+}
+
 int do_set_points(nufft_plan_s* p, int64_t m, const float* omega, cudaStream_t s) {
     if (m < 0 || m > (int64_t)INT32_MAX) return fail(NUFFT_ERR_INVALID_ARG, "m out of range");
     if (m > 0 && !omega) return fail(NUFFT_ERR_INVALID_ARG, "omega is NULL");
     if (m > p->M_cap) {
         NJ_CUDA(cudaStreamSynchronize(s));
+        if (p->aux) NJ_CUDA(cudaStreamSynchronize(p->aux));
         int st = alloc_points(p, m);
         if (st) return st;
         p->bytes = 0;
     }
     p->M = m;
     p->last_stream = s;
-    SortArgs a = sort_args(p, omega);
-    int st;
-    // the histogram is cleared only when fresh: every bin scan leaves it zero for the next sort
-    if (!p->kcount_clear &&
-        (st = launch(p, PK_ZERO, s, [&] { return launch_zero(p->d_kcount, sizeof(int) * p->nbins, s); })))
-        return st;
-    p->kcount_clear = false;
-    if ((st = launch(p, PK_BIN_COUNT, s, [&] { return launch_key_count(a, s); }))) return st;
-    if (p->nbins <= kFusedTablesMaxBins) {
-        if ((st = launch(p, PK_BIN_SCAN, s, [&] { return launch_sort_tables(a, s); }))) return st;
-        p->kcount_clear = true;
+    // the plan keeps its own copy of omega (the caller's buffer is free once the copy has run);
+    // the sort itself runs in the next call that needs the points (sort_rest)
+    if (m > 0) NJ_CUDA(cudaMemcpyAsync(p->d_om, omega, sizeof(float) * p->D * m, cudaMemcpyDeviceToDevice, s));
+    unsigned long long id = 0;
+    if (capture_id(s, id)) {
+        p->cap_id = id;
+        p->cap_pending = true;
     } else {
-        if ((st = launch(p, PK_BIN_SCAN, s, [&] { return launch_bin_scan(a, s); }))) return st;
-        p->kcount_clear = true;
-        if ((st = launch(p, PK_TILE_SCAN, s, [&] { return launch_tile_lists(a, s); }))) return st;
-        if ((st = launch(p, PK_BIN_ITEMS, s, [&] { return launch_item_scan(a, s); }))) return st;
+        p->sort_pending = true;
     }
-    if ((st = launch(p, PK_BIN_SCATTER, s, [&] { return launch_bin_scatter(a, s); }))) return st;
+    if (!p->aux) return sort_rest(p, s);   // plans without a stream of their own sort in line
+    return NUFFT_OK;
+}
+
+// The sort of the plan's copy of omega: histogram, scan, tile lists and items, scatter of the point
+// records and weights; on the plan's stream, forked from s and joined by sort_join, when the plan
+// has one.  An eager call sorts what the last eager set_points left; a call recorded into a graph
+// sorts when that graph, or the eager state, has points not yet sorted, and then clears the
+// histogram itself, so that every replay sorts completely.
+int sort_rest(nufft_plan_s* p, cudaStream_t s) {
+    unsigned long long id = 0;
+    const bool capturing = capture_id(s, id);
+    bool run;
+    if (capturing) {
+        run = (p->cap_pending && p->cap_id == id) || p->sort_pending;
+        if (p->cap_id == id) p->cap_pending = false;
+    } else {
+        run = p->sort_pending;
+        p->sort_pending = false;
+    }
+    if (!run) return NUFFT_OK;
+    SortArgs a = sort_args(p, p->d_om);
+    cudaStream_t ss = s;
+    if (p->aux) {
+        NJ_CUDA(cudaEventRecord(p->fork_ev, s));
+        NJ_CUDA(cudaStreamWaitEvent(p->aux, p->fork_ev, 0));
+        ss = p->aux;
+    }
+    int st;
+    // every scan leaves the histogram zero for the next sort; a fresh one, or one in a graph, is cleared
+    if ((capturing || !p->kcount_clear) &&
+        (st = launch(p, PK_ZERO, ss, [&] { return launch_zero(p->d_kcount, sizeof(int) * p->nbins, ss); })))
+        return st;
+    if ((st = launch(p, PK_BIN_COUNT, ss, [&] { return launch_key_count(a, ss); }))) return st;
+    if (p->nbins <= kFusedTablesMaxBins) {
+        if ((st = launch(p, PK_BIN_SCAN, ss, [&] { return launch_sort_tables(a, ss); }))) return st;
+    } else {
+        if ((st = launch(p, PK_BIN_SCAN, ss, [&] { return launch_bin_scan(a, ss); }))) return st;
+        if ((st = launch(p, PK_TILE_SCAN, ss, [&] { return launch_tile_lists(a, ss); }))) return st;
+        if ((st = launch(p, PK_BIN_ITEMS, ss, [&] { return launch_item_scan(a, ss); }))) return st;
+    }
+    if (!capturing) p->kcount_clear = true;
+    if ((st = launch(p, PK_BIN_SCATTER, ss, [&] { return launch_bin_scatter(a, ss); }))) return st;
+    if (p->aux) {
+        NJ_CUDA(cudaEventRecord(p->join_ev, p->aux));
+        p->join_pending = true;
+    }
+    return NUFFT_OK;
+}
+
+// Makes s wait for the sort before a kernel that reads the sorted points.
+int sort_join(nufft_plan_s* p, cudaStream_t s) {
+    if (!p->join_pending) return NUFFT_OK;
+    p->join_pending = false;
+    NJ_CUDA(cudaStreamWaitEvent(s, p->join_ev, 0));
     return NUFFT_OK;
 }
 
@@ -703,6 +778,13 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
     if (cudaMalloc(&p->d_G, p->G_elems * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&p->d_T, p->T_elems * sizeof(float2)) != cudaSuccess)
         return oom("workspace");
+    if (cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(p);
+        return fail(NUFFT_ERR_CUDA, "stream or event creation failed");
+    }
     if ((st = alloc_points(p, std::max<int64_t>(m, 1)))) { free_plan(p); return st; }
     if ((st = do_set_points(p, m, omega, (cudaStream_t)stream))) { free_plan(p); return st; }
     *out = p;
@@ -721,8 +803,10 @@ int nufft_forward(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cflo
     if (!x || (!y && p->M > 0)) return fail(NUFFT_ERR_INVALID_ARG, "x or y is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
-    if (p->M == 0) return NUFFT_OK;
+    if ((st = sort_rest(p, s))) return st;
+    if (p->M == 0) return sort_join(p, s);
     if ((st = forward_grids(p, C, 1, 1, (const float2*)x, (const float2*)smaps, s))) return st;
+    if ((st = sort_join(p, s))) return st;
     GatherArgs g = gather_args(p, C, 1, 1);
     g.y = (float2*)y;
     const int cpl = gather_cpl(g);
@@ -736,6 +820,7 @@ int nufft_adjoint(nufft_plan_t p, int C, const nufft_cfloat* y, const nufft_cflo
     if (!x || (!y && p->M > 0)) return fail(NUFFT_ERR_INVALID_ARG, "x or y is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
+    if ((st = sort_rest(p, s)) || (st = sort_join(p, s))) return st;
     return adjoint_impl(p, C, (const float2*)y, (const float2*)smaps, (float2*)x, s);
 }
 
@@ -746,10 +831,12 @@ int nufft_jvp_omega(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cf
     if (!x || (p->M > 0 && (!domega || !dy))) return fail(NUFFT_ERR_INVALID_ARG, "x, domega or dy is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
-    if (p->M == 0) return NUFFT_OK;
+    if ((st = sort_rest(p, s))) return st;
+    if (p->M == 0) return sort_join(p, s);
     const int hp = y_or_null ? 1 : 0;
     const int nd = p->D + hp;
     if ((st = forward_grids(p, C, nd, hp, (const float2*)x, (const float2*)smaps, s))) return st;
+    if ((st = sort_join(p, s))) return st;
     GatherArgs g = gather_args(p, C, nd, hp);
     g.y = (float2*)y_or_null;
     g.dy = (float2*)dy;
@@ -768,8 +855,10 @@ int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_
     // With both outputs the gather also writes v in sorted point order into T (free once the
     // last forward pass has read it) for the adjoint's spread, which then needs no reorder pass.
     const float2* vsorted = nullptr;
+    if ((st = sort_rest(p, s))) return st;
     if (grad_omega && p->M > 0) {
         if ((st = forward_grids(p, C, p->D, 0, (const float2*)x, (const float2*)smaps, s))) return st;
+        if ((st = sort_join(p, s))) return st;
         GatherArgs g = gather_args(p, C, p->D, 0);
         g.v = (const float2*)v;
         g.grad = grad_omega;
@@ -780,6 +869,7 @@ int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_
         const int cpl = gather_cpl(g);
         if ((st = launch(p, PK_GATHER_VJP, s, [&] { return launch_gather(GM_VJP, g, cpl, s); }))) return st;
     }
+    if ((st = sort_join(p, s))) return st;
     if (grad_x) return adjoint_impl(p, C, (const float2*)v, (const float2*)smaps, (float2*)grad_x, s, vsorted);
     return NUFFT_OK;
 }
@@ -807,6 +897,7 @@ void nufft_destroy(nufft_plan_t p) {
     if (!p) return;
     if (p->last_stream) cudaStreamSynchronize(p->last_stream);
     else cudaDeviceSynchronize();
+    if (p->aux) cudaStreamSynchronize(p->aux);
     free_plan(p);
 }
 
@@ -945,6 +1036,7 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
                  o_nitems = cv.take<int>(1), o_items = cv.take<int4>(max_items(p, mc)), o_local = cv.take<int>(mc),
                  o_keyid = cv.take<int>(mc), o_pidx = cv.take<int4>(mc), o_pfrac = cv.take<float4>(mc),
                  o_pw = cv.take<float>((size_t)mc * p.ws),
+                 o_om = cv.take<float>((size_t)mc * p.D),
                  o_G = cv.take<float2>(G), o_T = cv.take<float2>(T);
     if (cv.off > (size_t)NUFFT_NOALLOC_SCRATCH_BYTES)
         return fail(NUFFT_ERR_UNSUPPORTED, "problem needs " + std::to_string(cv.off) +
@@ -985,6 +1077,7 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
     p.d_pidx = (int4*)(b + o_pidx);
     p.d_pfrac = (float4*)(b + o_pfrac);
     p.d_pw = (float*)(b + o_pw);
+    p.d_om = (float*)(b + o_om);
     p.d_G = (float2*)(b + o_G);
     p.d_T = (float2*)(b + o_T);
     p.G_elems = G;

@@ -60,3 +60,53 @@ def test_graph_replay_matches_eager_step_and_follows_new_omega():
     assert np.array_equal(replayed[0], fresh[0]) and np.array_equal(replayed[1], fresh[1])
     assert rel(replayed[2], fresh[2]) < 1e-6
     assert rel(fresh[0], ref[0]) > 0.1                 # the locations did change the result
+
+
+def test_forward_captured_alone_after_eager_set_points_replays_correctly():
+    """Only the forward is captured: the sort it completes must stay outside the graph."""
+    import torch
+
+    from paper_2111_02912_gb300 import Plan
+    shape, M, C = (40, 32), 2500, 3
+    case = make_case(shape, M, C, True, seed=63)
+    om = to_dev(case["omega"])
+    X, S = to_dev(case["x"]), to_dev(case["smaps"])
+    plan = Plan(shape, om, max_coils=C)
+    y = torch.empty((C, M), dtype=torch.complex64, device=om.device)
+    plan.forward(X, S, out=y)
+    torch.cuda.synchronize()
+    ref = host(y).copy()
+    plan.set_points(om)                              # eager; the rest of the sort is still pending
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.forward(X, S, out=y)                    # warm-up outside the capture
+    torch.cuda.current_stream().wait_stream(side)
+    plan.set_points(om)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.forward(X, S, out=y)
+    for _ in range(3):
+        y.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(host(y), ref)
+
+
+def test_set_points_twice_before_use():
+    """A histogram that was never scanned is cleared by the next set_points."""
+    import torch
+
+    from paper_2111_02912_gb300 import Plan
+    shape, M, C = (32, 32), 2000, 2
+    case = make_case(shape, M, C, True, seed=64)
+    om = to_dev(case["omega"])
+    X, S = to_dev(case["x"]), to_dev(case["smaps"])
+    plan = Plan(shape, om, max_coils=C)
+    ref = host(plan.forward(X, S)).copy()
+    other = torch.from_numpy(np.random.default_rng(65).uniform(-np.pi, np.pi, (2, M)).astype(np.float32)).to(om.device)
+    plan.set_points(other)
+    plan.set_points(om)
+    y = host(plan.forward(X, S))
+    torch.cuda.synchronize()
+    assert np.array_equal(y, ref)
