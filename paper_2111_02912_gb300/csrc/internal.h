@@ -10,7 +10,7 @@ namespace nj {
 // ---------------------------------------------------------------- sorting
 // Points are ordered by the bin (a tile of B_d cells per axis) of their window
 // start; each bin is a contiguous range.
-constexpr int kNbrStride = 64;        // ints per tile in tile_nbr: n, then 27 (start, prefix) pairs, total
+constexpr int kNbrStride = 64;        // entries per tile in tile_nbr: n, then 27 (start, prefix) pairs, total
 
 struct SortArgs {
     const float* omega;   // [D][M]
@@ -27,7 +27,8 @@ struct SortArgs {
     int* item_off;    // [nbins + 1]  first spread work item of each tile
     int* tile_parts;  // [nbins]      spread work items of each tile
     int* heavy;       // [nbins + 1]  count, then the tiles with more than one work item (any order)
-    int* tile_nbr;    // [nbins][kNbrStride]  bins that reach the tile: count, then (start, prefix) pairs
+    int* tile_nbr;    // [kNbrStride][nbins]  bins that reach the tile: count, then (start, prefix) pairs
+                      //                      (entry-major: the stores of neighbouring tiles coalesce)
     int4* items;      // [max_items]  {tile, part, nparts, 0}
     int* nitems;      // [1]
     int4* pidx;       // [M]
@@ -49,11 +50,11 @@ cudaError_t launch_bin_scatter(const SortArgs& a, cudaStream_t s);   // records 
 // covers J cells to the right of its start, so along each axis these are the
 // tile's own bin and the bins holding the J-1 cells before its first cell
 // (periodic; at most three, without repeats).  Writes the tile's list entry,
-// tn[0] = count, then (first point, candidate prefix) pairs and the total, and
-// returns the candidate count.  Every array index is fixed after unrolling, so
+// tn[0] = count, then (first point, candidate prefix) pairs and the total, entry
+// k at tn[k * stride], and returns the candidate count.  Every array index is fixed after unrolling, so
 // nothing goes to local memory.
 __device__ __forceinline__ int tile_bin_list(int D, const int* nb, const int* B, const int* K, int J, int bin,
-                                             const int* offsets, int* tn) {
+                                             const int* offsets, int* tn, int stride) {
     int x[kMaxDim][3], n[kMaxDim];
     int r = bin;
 #pragma unroll
@@ -94,15 +95,15 @@ __device__ __forceinline__ int tile_bin_list(int D, const int* nb, const int* B,
                     if (D > 1) id = id * nb[1] + x[1][i1];
                     if (D > 2) id = id * nb[2] + x[2][i2];
                     const int st = offsets[id];
-                    tn[1 + 2 * q] = st;
-                    tn[2 + 2 * q] = cand;
+                    tn[(int64_t)(1 + 2 * q) * stride] = st;
+                    tn[(int64_t)(2 + 2 * q) * stride] = cand;
                     cand += offsets[id + 1] - st;
                     ++q;
                 }
             }
     tn[0] = q;
-    tn[1 + 2 * q] = 0;
-    tn[2 + 2 * q] = cand;
+    tn[(int64_t)(1 + 2 * q) * stride] = 0;
+    tn[(int64_t)(2 + 2 * q) * stride] = cand;
     return cand;
 }
 
@@ -194,7 +195,7 @@ struct SpreadArgs {
     int B[kMaxDim], nb[kMaxDim];   // tile (= bin) edge, tiles per dim
     int nbins;
     const int* offsets;   // [nbins + 1]
-    const int* tile_nbr;  // [nbins][kNbrStride]
+    const int* tile_nbr;  // [kNbrStride][nbins], entry-major
     const int4* items;    // spread work items {tile, part, nparts, candidates}
     const int* nitems;
     const int* tile_parts;

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(1024) k_bin_scan(SortArgs a) {
 __global__ void k_tile_lists(SortArgs a) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= a.nbins) return;
-    const int cand = tile_bin_list(a.D, a.nb, a.B, a.K, a.J, b, a.offsets, a.tile_nbr + (int64_t)b * kNbrStride);
+    const int cand = tile_bin_list(a.D, a.nb, a.B, a.K, a.J, b, a.offsets, a.tile_nbr + b, a.nbins);
     a.tile_parts[b] = max(1, (cand + a.P - 1) / a.P);
 }
 
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(1024) k_sort_tables(SortArgs a) {
     __syncthreads();   // offsets are read by other threads below (global, same block)
     int parts_sum = 0;
     for (int b = lo; b < hi; ++b) {
-        const int cand = tile_bin_list(a.D, a.nb, a.B, a.K, a.J, b, a.offsets, a.tile_nbr + (int64_t)b * kNbrStride);
+        const int cand = tile_bin_list(a.D, a.nb, a.B, a.K, a.J, b, a.offsets, a.tile_nbr + b, a.nbins);
         const int parts = max(1, (cand + a.P - 1) / a.P);
         a.tile_parts[b] = parts;
         parts_sum += parts;

@@ -73,10 +73,11 @@ __global__ void __launch_bounds__(256, 2) k_spread(SpreadArgs a) {
     float2* tl = (float2*)smem4;   // [tcells][CC]
 
     {   // bins that reach this tile (listed by the sort)
-        const int* tn = a.tile_nbr + (int64_t)tile * kNbrStride;
+        const int* tn = a.tile_nbr + tile;
+        const int64_t st = a.nbins;
         if (tid == 0) s_nn = tn[0];
-        if (tid < 27) s_start[tid] = tn[1 + 2 * tid];      // entries past the count are never used
-        if (tid < 28) s_pref[tid] = tn[2 + 2 * tid];
+        if (tid < 27) s_start[tid] = tn[(1 + 2 * tid) * st];      // entries past the count are never used
+        if (tid < 28) s_pref[tid] = tn[(2 + 2 * tid) * st];
     }
     {   // clear the tile
         float4* t4 = (float4*)tl;
@@ -307,10 +308,11 @@ __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
     int* s_tmp = s_cur + NK;       // [P] hits in arrival order within their start cells
 
     {
-        const int* tn = a.tile_nbr + (int64_t)tile * kNbrStride;
+        const int* tn = a.tile_nbr + tile;
+        const int64_t st = a.nbins;
         if (tid == 0) { s_nn = tn[0]; s_nh = 0; }
-        if (tid < 27) s_start[tid] = tn[1 + 2 * tid];      // entries past the count are never used
-        if (tid < 28) s_pref[tid] = tn[2 + 2 * tid];
+        if (tid < 27) s_start[tid] = tn[(1 + 2 * tid) * st];      // entries past the count are never used
+        if (tid < 28) s_pref[tid] = tn[(2 + 2 * tid) * st];
     }
     for (int i = tid; i <= NK; i += nt) s_cnt[i] = 0;
     __syncthreads();
@@ -546,10 +548,11 @@ __global__ void __launch_bounds__(512) k_spread_rows(SpreadArgs a) {
     int4 item = a.items[it];
     int tn0 = 0, tn1 = 0, tn2 = 0;   // this thread's entries of the tile's bin list
     {
-        const int* tn = a.tile_nbr + (int64_t)item.x * kNbrStride;
+        const int* tn = a.tile_nbr + item.x;
+        const int64_t st = a.nbins;
         if (tid == 0) tn0 = tn[0];
-        if (tid < 27) tn1 = tn[1 + 2 * tid];
-        if (tid < 28) tn2 = tn[2 + 2 * tid];
+        if (tid < 27) tn1 = tn[(1 + 2 * tid) * st];
+        if (tid < 28) tn2 = tn[(2 + 2 * tid) * st];
     }
     for (;;) {
         const int itn = it + (int)gridDim.x;
@@ -645,10 +648,11 @@ __global__ void __launch_bounds__(512) k_spread_rows(SpreadArgs a) {
             atomicAdd(&s_cur[bk], 1);
         }
         if (itn < nitems) {   // the next item's bin list, consumed at its start
-            const int* tn = a.tile_nbr + (int64_t)itemn.x * kNbrStride;
+            const int* tn = a.tile_nbr + itemn.x;
+            const int64_t st = a.nbins;
             if (tid == 0) tn0 = tn[0];
-            if (tid < 27) tn1 = tn[1 + 2 * tid];
-            if (tid < 28) tn2 = tn[2 + 2 * tid];
+            if (tid < 27) tn1 = tn[(1 + 2 * tid) * st];
+            if (tid < 28) tn2 = tn[(2 + 2 * tid) * st];
         }
         __syncthreads();
         // exclusive scan of the bucket counts (one warp)

@@ -778,7 +778,13 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
     if (cudaMalloc(&p->d_G, p->G_elems * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&p->d_T, p->T_elems * sizeof(float2)) != cudaSuccess)
         return oom("workspace");
-    if (cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
+    // the sort is short and on the path to the first gather: its blocks go before queued FFT blocks
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+        cudaGetLastError();
+        prio_hi = 0;
+    }
+    if (cudaStreamCreateWithPriority(&p->aux, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
