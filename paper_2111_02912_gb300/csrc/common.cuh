@@ -89,4 +89,33 @@ inline void ensure_smem(size_t bytes) {
     }
 }
 
+
+// Programmatic dependent launch (sm_90 and later).  Kernels are launched with programmatic stream
+// serialization, so the launch of a kernel is processed while the kernel before it in the stream
+// still runs, and every kernel starts with pdl_wait(): griddepcontrol.wait blocks until that
+// previous kernel has completed and its memory operations are visible (at once for a kernel
+// launched without the attribute).  Every global access thus still follows the previous kernel's
+// completion; only the launch gap between them shrinks.  No kernel signals its dependents early
+// (griddepcontrol.launch_dependents): blocks parked on the wait held SM slots that a concurrent
+// stream's kernels needed (measured: replayed radial320 step 0.2895 -> 0.3037 ms with an early
+// signal, 0.2857 ms without; eager step 0.3126 -> 0.2887 ms).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+// Launches kernel<<<grid, block, smem, s>>>(args...) with programmatic stream serialization.
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace nj

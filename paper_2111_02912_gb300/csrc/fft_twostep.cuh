@@ -50,6 +50,7 @@ __device__ __forceinline__ void image_row_factors(const ImageSide& im, int64_t b
 
 template <int L1, int L2, PassKind KIND>
 __global__ void __launch_bounds__(512, 1) k_line_fft2(LinePass a) {
+    pdl_wait();
     constexpr int DIR = (KIND == PASS_FWD_FIRST || KIND == PASS_FWD_MID) ? -1 : 1;
     constexpr int L = L1 * L2;
     constexpr int RP = L2 + 1;   // row pitch inside a line
@@ -277,7 +278,7 @@ cudaError_t launch_fft2_kind(int L1, int L2, const LinePass& a, dim3 grid, int t
 #define NJ_FFT2_CASE(A, B)                                                  \
     if (L1 == A && L2 == B) {                                                \
         ensure_smem<k_line_fft2<A, B, KIND>>(smem);                          \
-        k_line_fft2<A, B, KIND><<<grid, threads, smem, s>>>(a);              \
+        (void)launch_pdl(k_line_fft2<A, B, KIND>, grid, threads, smem, s, a);              \
         return cudaGetLastError();                                           \
     }
     NJ_FFT2_SIZES(NJ_FFT2_CASE)

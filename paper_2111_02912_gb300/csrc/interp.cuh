@@ -191,6 +191,7 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a) {
 
 template <int D, int J, int ND, int CPL, int MODE, bool PAIR>
 __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
+    pdl_wait();
     gather_body<D, J, ND, CPL, MODE, PAIR>(a);
 }
 
@@ -199,6 +200,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
 // case.  The forward at 40 or 48 registers spills and gains nothing; the other VJP kinds spill at 64.
 template <int D, int J, int ND, int CPL, int MODE, bool PAIR>
 __global__ void __launch_bounds__(256, 4) k_gather_occ4(GatherArgs a) {
+    pdl_wait();
     gather_body<D, J, ND, CPL, MODE, PAIR>(a);
 }
 
@@ -210,11 +212,11 @@ static cudaError_t gather_cpl(const GatherArgs& a, int cpl, cudaStream_t s) {
     const size_t smem = (size_t)gpb * D * J * sizeof(float);
     if (blocks == 0) return cudaSuccess;
     if (cpl == 0) {   // coil pairs
-        if constexpr (D == 2 && MODE == GM_VJP) k_gather_occ4<D, J, ND, 1, MODE, true><<<blocks, threads, smem, s>>>(a);
-        else k_gather<D, J, ND, 1, MODE, true><<<blocks, threads, smem, s>>>(a);
+        if constexpr (D == 2 && MODE == GM_VJP) (void)launch_pdl(k_gather_occ4<D, J, ND, 1, MODE, true>, blocks, threads, smem, s, a);
+        else (void)launch_pdl(k_gather<D, J, ND, 1, MODE, true>, blocks, threads, smem, s, a);
     }
-    else if (cpl == 1) k_gather<D, J, ND, 1, MODE, false><<<blocks, threads, smem, s>>>(a);
-    else k_gather<D, J, ND, 4, MODE, false><<<blocks, threads, smem, s>>>(a);   // C up to 4 G = 128
+    else if (cpl == 1) (void)launch_pdl(k_gather<D, J, ND, 1, MODE, false>, blocks, threads, smem, s, a);
+    else (void)launch_pdl(k_gather<D, J, ND, 4, MODE, false>, blocks, threads, smem, s, a);   // C up to 4 G = 128
     return cudaGetLastError();
 }
 

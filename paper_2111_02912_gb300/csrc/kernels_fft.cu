@@ -167,6 +167,7 @@ __device__ __forceinline__ void image_row(int D, int N0, int N1, const float* de
 
 template <PassKind KIND>
 __global__ void __launch_bounds__(256) k_line_fft(LinePass a) {
+    pdl_wait();
     constexpr int DIR = (KIND == PASS_FWD_FIRST || KIND == PASS_FWD_MID) ? -1 : 1;
     extern __shared__ float2 smem[];
     const int L = a.ax.L;
@@ -300,6 +301,7 @@ __global__ void __launch_bounds__(256) k_line_fft(LinePass a) {
 }
 
 __global__ void k_sum_chunks(const float2* __restrict__ part, int nparts, int64_t n, float2* __restrict__ x) {
+    pdl_wait();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         float2 acc = part[i];
@@ -310,7 +312,7 @@ __global__ void k_sum_chunks(const float2* __restrict__ part, int nparts, int64_
 
 cudaError_t launch_sum_chunks(const float2* part, int nparts, int64_t n, float2* x, cudaStream_t s) {
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
-    k_sum_chunks<<<blocks, 256, 0, s>>>(part, nparts, n, x);
+    (void)launch_pdl(k_sum_chunks, blocks, 256, 0, s, part, nparts, n, x);
     return cudaGetLastError();
 }
 
@@ -319,19 +321,19 @@ cudaError_t launch_line_pass(PassKind kind, const LinePass& a, dim3 grid, int th
     switch (kind) {
         case PASS_FWD_FIRST:
             ensure_smem<k_line_fft<PASS_FWD_FIRST>>(smem);
-            k_line_fft<PASS_FWD_FIRST><<<grid, threads, smem, s>>>(a);
+            (void)launch_pdl(k_line_fft<PASS_FWD_FIRST>, grid, threads, smem, s, a);
             break;
         case PASS_FWD_MID:
             ensure_smem<k_line_fft<PASS_FWD_MID>>(smem);
-            k_line_fft<PASS_FWD_MID><<<grid, threads, smem, s>>>(a);
+            (void)launch_pdl(k_line_fft<PASS_FWD_MID>, grid, threads, smem, s, a);
             break;
         case PASS_INV_MID:
             ensure_smem<k_line_fft<PASS_INV_MID>>(smem);
-            k_line_fft<PASS_INV_MID><<<grid, threads, smem, s>>>(a);
+            (void)launch_pdl(k_line_fft<PASS_INV_MID>, grid, threads, smem, s, a);
             break;
         case PASS_INV_LAST:
             ensure_smem<k_line_fft<PASS_INV_LAST>>(smem);
-            k_line_fft<PASS_INV_LAST><<<grid, threads, smem, s>>>(a);
+            (void)launch_pdl(k_line_fft<PASS_INV_LAST>, grid, threads, smem, s, a);
             break;
     }
     return cudaGetLastError();

@@ -54,6 +54,7 @@ __device__ __forceinline__ void point_record(const SortArgs& a, int64_t i, int4&
 }
 
 __global__ void k_zero(float4* p, int64_t n4, int* tail, int64_t ntail) {
+    pdl_wait();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride)
         p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -65,6 +66,7 @@ __global__ void k_zero(float4* p, int64_t n4, int* tail, int64_t ntail) {
 // same bin take one atomic between them: the group leader adds the group size
 // and the others offset from the returned base by their rank in the group.
 __global__ void k_key_count(SortArgs a) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < a.m;
     int key = -1;
@@ -118,6 +120,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& excl) {
 // Each thread scans a contiguous chunk; the counts are cleared on the way, so
 // the next sort needs no clearing pass.
 __global__ void __launch_bounds__(1024) k_bin_scan(SortArgs a) {
+    pdl_wait();
     __shared__ int sh[32];
     const int n = a.nbins;
     const int per = (n + 1023) / 1024;
@@ -142,6 +145,7 @@ __global__ void __launch_bounds__(1024) k_bin_scan(SortArgs a) {
 // cells before it, at most 3^D), their point ranges as one candidate list, and
 // the number of spread work items (candidates / P, at least one).
 __global__ void k_tile_lists(SortArgs a) {
+    pdl_wait();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= a.nbins) return;
     const int cand = tile_bin_list(a.D, a.nb, a.B, a.K, a.J, b, a.offsets, a.tile_nbr + b, a.nbins);
@@ -151,6 +155,7 @@ __global__ void k_tile_lists(SortArgs a) {
 // One block: exclusive scan of the work items per tile, and the item list
 // {tile, part, parts, 0}.
 __global__ void __launch_bounds__(1024) k_item_scan(SortArgs a) {
+    pdl_wait();
     __shared__ int sh[32];
     const int n = a.nbins;
     const int per = (n + 1023) / 1024;
@@ -175,6 +180,7 @@ __global__ void __launch_bounds__(1024) k_item_scan(SortArgs a) {
 // All three tables in one block when the bins are few (one launch instead of
 // three): bin offsets, the tiles' reaching bins and parts, item offsets and list.
 __global__ void __launch_bounds__(1024) k_sort_tables(SortArgs a) {
+    pdl_wait();
     __shared__ int sh[32];
     const int n = a.nbins, t = threadIdx.x;
     const int per = (n + 1023) / 1024;
@@ -216,6 +222,7 @@ __global__ void __launch_bounds__(1024) k_sort_tables(SortArgs a) {
 }
 
 __global__ void k_bin_scatter(SortArgs a) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.m) return;
     int4 ix;
@@ -238,33 +245,33 @@ cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s) {
     const int64_t ntail = (int64_t)((bytes - n4 * 16) / 4);
     int blocks = (int)std::min<int64_t>((n4 + 255) / 256, 152 * 16);
     if (blocks < 1) blocks = 1;
-    k_zero<<<blocks, 256, 0, s>>>((float4*)p, n4, (int*)((char*)p + n4 * 16), ntail);
+    (void)launch_pdl(k_zero, blocks, 256, 0, s, (float4*)p, n4, (int*)((char*)p + n4 * 16), ntail);
     return cudaGetLastError();
 }
 cudaError_t launch_key_count(const SortArgs& a, cudaStream_t s) {
     if (a.m == 0) return cudaSuccess;
-    k_key_count<<<(unsigned)((a.m + 255) / 256), 256, 0, s>>>(a);
+    (void)launch_pdl(k_key_count, (unsigned)((a.m + 255) / 256), 256, 0, s, a);
     return cudaGetLastError();
 }
 cudaError_t launch_bin_scan(const SortArgs& a, cudaStream_t s) {
-    k_bin_scan<<<1, 1024, 0, s>>>(a);
+    (void)launch_pdl(k_bin_scan, 1, 1024, 0, s, a);
     return cudaGetLastError();
 }
 cudaError_t launch_sort_tables(const SortArgs& a, cudaStream_t s) {
-    k_sort_tables<<<1, 1024, 0, s>>>(a);
+    (void)launch_pdl(k_sort_tables, 1, 1024, 0, s, a);
     return cudaGetLastError();
 }
 cudaError_t launch_tile_lists(const SortArgs& a, cudaStream_t s) {
-    k_tile_lists<<<(a.nbins + 127) / 128, 128, 0, s>>>(a);
+    (void)launch_pdl(k_tile_lists, (a.nbins + 127) / 128, 128, 0, s, a);
     return cudaGetLastError();
 }
 cudaError_t launch_item_scan(const SortArgs& a, cudaStream_t s) {
-    k_item_scan<<<1, 1024, 0, s>>>(a);
+    (void)launch_pdl(k_item_scan, 1, 1024, 0, s, a);
     return cudaGetLastError();
 }
 cudaError_t launch_bin_scatter(const SortArgs& a, cudaStream_t s) {
     if (a.m == 0) return cudaSuccess;
-    k_bin_scatter<<<(unsigned)((a.m + 255) / 256), 256, 0, s>>>(a);
+    (void)launch_pdl(k_bin_scatter, (unsigned)((a.m + 255) / 256), 256, 0, s, a);
     return cudaGetLastError();
 }
 

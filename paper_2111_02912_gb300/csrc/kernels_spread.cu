@@ -42,6 +42,7 @@ constexpr int kSpreadCoilsPerWarp = 16;   // y staging per warp: 32 candidates x
 
 template <int D, int J>
 __global__ void __launch_bounds__(256, 2) k_spread(SpreadArgs a) {
+    pdl_wait();
     using SH = SpreadShape<D, J>;
     constexpr int JO = SH::JO, JI = SH::JI, NR = SH::NR;
     extern __shared__ float4 smem4[];
@@ -268,6 +269,7 @@ __global__ void __launch_bounds__(256, 2) k_spread(SpreadArgs a) {
 // differences).
 template <int D, int J, int CPT>
 __global__ void __launch_bounds__(512) k_spread_cells(SpreadArgs a) {
+    pdl_wait();
     extern __shared__ float4 smem4[];
     __shared__ int s_start[27], s_pref[28], s_nn, s_nh;
     const int it = blockIdx.x;
@@ -487,13 +489,13 @@ static cudaError_t spread_cells_cpt(const SpreadArgs& a, cudaStream_t s, int thr
     dim3 grid((unsigned)a.max_items, (unsigned)((a.C + cpt - 1) / cpt));
     if (cpt <= 4) {
         ensure_smem<k_spread_cells<D, J, 4>>(smem);
-        k_spread_cells<D, J, 4><<<grid, threads, smem, s>>>(a);
+        (void)launch_pdl(k_spread_cells<D, J, 4>, grid, threads, smem, s, a);
     } else if (cpt <= 8) {
         ensure_smem<k_spread_cells<D, J, 8>>(smem);
-        k_spread_cells<D, J, 8><<<grid, threads, smem, s>>>(a);
+        (void)launch_pdl(k_spread_cells<D, J, 8>, grid, threads, smem, s, a);
     } else {
         ensure_smem<k_spread_cells<D, J, 16>>(smem);
-        k_spread_cells<D, J, 16><<<grid, threads, smem, s>>>(a);
+        (void)launch_pdl(k_spread_cells<D, J, 16>, grid, threads, smem, s, a);
     }
     return cudaGetLastError();
 }
@@ -536,6 +538,7 @@ static cudaError_t launch_spread_cells_3d(const SpreadArgs& a, cudaStream_t s) {
 // sums follows the (arrival-ordered) hit list, so results agree to rounding.
 template <int D, int J, int CPT>
 __global__ void __launch_bounds__(512) k_spread_rows(SpreadArgs a) {
+    pdl_wait();
     extern __shared__ float4 smem4[];
     __shared__ int s_start[27], s_pref[28], s_nn, s_nh;
     const int nitems = a.nitems[0];
@@ -839,13 +842,13 @@ static cudaError_t spread_rows_cpt(const SpreadArgs& a, cudaStream_t s, int thre
     dim3 grid((unsigned)std::min<int64_t>(a.max_items, 2 * (int64_t)device_sms()), (unsigned)((a.C + cpt - 1) / cpt));
     if (cpt == 4) {
         ensure_smem<k_spread_rows<D, J, 4>>(smem);
-        k_spread_rows<D, J, 4><<<grid, threads, smem, s>>>(a);
+        (void)launch_pdl(k_spread_rows<D, J, 4>, grid, threads, smem, s, a);
     } else if (cpt == 8) {
         ensure_smem<k_spread_rows<D, J, 8>>(smem);
-        k_spread_rows<D, J, 8><<<grid, threads, smem, s>>>(a);
+        (void)launch_pdl(k_spread_rows<D, J, 8>, grid, threads, smem, s, a);
     } else {
         ensure_smem<k_spread_rows<D, J, 16>>(smem);
-        k_spread_rows<D, J, 16><<<grid, threads, smem, s>>>(a);
+        (void)launch_pdl(k_spread_rows<D, J, 16>, grid, threads, smem, s, a);
     }
     return cudaGetLastError();
 }
@@ -877,6 +880,7 @@ cudaError_t launch_spread_cells(const SpreadArgs& a, cudaStream_t s) {
 // Clears the cells (all coils) of the tiles that are split over several work items.
 __global__ void k_permute_y(const int4* __restrict__ idx, const float2* __restrict__ y, float2* __restrict__ ys,
                             int64_t M, int C) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     const int64_t o = idx[i].w;
@@ -893,13 +897,14 @@ __global__ void k_permute_y(const int4* __restrict__ idx, const float2* __restri
 
 cudaError_t launch_permute_y(const int4* idx, const float2* y, float2* ys, int64_t M, int C, cudaStream_t s) {
     if (M == 0) return cudaSuccess;
-    k_permute_y<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(idx, y, ys, M, C);
+    (void)launch_pdl(k_permute_y, (unsigned)((M + 255) / 256), 256, 0, s, idx, y, ys, M, C);
     return cudaGetLastError();
 }
 
 // The sort lists these tiles; blocks walk the list, warps take tile rows (all axes but the
 // last), and each row's cells times coils are one contiguous run of the grid.
 __global__ void k_zero_heavy_tiles(SpreadArgs a) {
+    pdl_wait();
     const int nh = a.heavy[0];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = blockIdx.x; i < nh; i += gridDim.x) {
@@ -928,7 +933,7 @@ __global__ void k_zero_heavy_tiles(SpreadArgs a) {
 template <int D, int J>
 static cudaError_t spread_j(const SpreadArgs& a, cudaStream_t s, size_t smem, dim3 grid) {
     ensure_smem<k_spread<D, J>>(smem);
-    k_spread<D, J><<<grid, 256, smem, s>>>(a);
+    (void)launch_pdl(k_spread<D, J>, grid, 256, smem, s, a);
     return cudaGetLastError();
 }
 
@@ -963,7 +968,7 @@ cudaError_t launch_spread(const SpreadArgs& a, int /*cpl*/, cudaStream_t s, size
 }
 
 cudaError_t launch_zero_heavy_tiles(const SpreadArgs& a, cudaStream_t s) {
-    k_zero_heavy_tiles<<<std::min(a.nbins, 152 * 4), 256, 0, s>>>(a);
+    (void)launch_pdl(k_zero_heavy_tiles, std::min(a.nbins, 152 * 4), 256, 0, s, a);
     return cudaGetLastError();
 }
 
