@@ -29,7 +29,10 @@
  *     same convention and grad_omega = dL/d omega exactly (no factor 2).
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All calls
  *     are asynchronous and stream-ordered; none synchronises the host except
- *     nufft_plan / nufft_set_points when the point capacity must grow.
+ *     nufft_plan / nufft_set_points when the point capacity must grow.  A plan
+ *     owns a second stream (highest priority) for its point sort: a call forks
+ *     it from `stream` and joins it back before returning, so every call is
+ *     self-contained and may be recorded into a CUDA graph.
  *   - Return NUFFT_OK (0) or a negative status.  Nothing is thrown across the
  *     ABI.  An asynchronous kernel fault is reported by a later call.
  *     nufft_last_error() gives a readable message for the calling thread.
@@ -82,8 +85,11 @@ void nufft_default_opts(nufft_opts* o, int dim, const int64_t* n);
  * depend on omega only).  m may be 0.  *out receives the plan. */
 int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* omega, void* stream);
 
-/* Re-sort after omega changed (every trajectory update).  m may differ from
- * the plan's current m; growing past the capacity reallocates (synchronising). */
+/* New sample locations (every trajectory update).  m may differ from the plan's
+ * current m; growing past the capacity reallocates (synchronising).  The call
+ * copies omega into the plan on `stream` (the caller's buffer is free once that
+ * copy has run); the bin sort itself runs in the next call that needs the
+ * points, on the plan's own stream, beside that call's FFT passes. */
 int nufft_set_points(nufft_plan_t p, int64_t m, const float* omega, void* stream);
 
 /* y[C][M] = E x: forward NUFFT of each coil image (Sec. II-B, II-G). */
