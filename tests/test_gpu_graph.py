@@ -110,3 +110,23 @@ def test_set_points_twice_before_use():
     y = host(plan.forward(X, S))
     torch.cuda.synchronize()
     assert np.array_equal(y, ref)
+
+
+def test_set_points_keeps_its_own_copy_of_omega():
+    """The caller may overwrite omega on the stream right after set_points: the sort reads the copy."""
+    import torch
+
+    from paper_2111_02912_gb300 import Plan
+    shape, M, C = (48, 32), 3000, 2
+    case = make_case(shape, M, C, True, seed=66)
+    om = to_dev(case["omega"])
+    X, S = to_dev(case["x"]), to_dev(case["smaps"])
+    ref = host(Plan(shape, om, max_coils=C).forward(X, S)).copy()
+    plan = Plan(shape, om, max_coils=C)
+    buf = om.clone()
+    plan.forward(X, S)                               # the plan's first sort is done
+    plan.set_points(buf)
+    buf.copy_(torch.from_numpy(np.random.default_rng(67).uniform(-np.pi, np.pi, (2, M)).astype(np.float32)))
+    y = host(plan.forward(X, S))
+    torch.cuda.synchronize()
+    assert np.array_equal(y, ref)
