@@ -48,12 +48,14 @@ __device__ __forceinline__ void image_row_factors(const ImageSide& im, int64_t b
     }
 }
 
-// Registers: 80 per thread, so that three 256-thread blocks share an SM (24 warps; the passes are
-// issue- and latency-bound): the register DFTs fit with at most a few bytes of spill (measured on
-// the 640-point passes: FWD_MID 37.6 -> 31.5 us, INV_MID 26.4 -> 22.4 us against 128 registers at
-// two blocks per SM).  The coil-summing INV_LAST runs 512-thread blocks and keeps 128.
+// Registers: with L2 = 32 (256-thread blocks of 8 lines) 80 per thread, so that three blocks share
+// an SM (24 warps; the passes are issue- and latency-bound): the register DFTs fit with at most a
+// few bytes of spill (measured on the 640-point passes: FWD_MID 37.6 -> 31.5 us, INV_MID 26.4 ->
+// 22.4 us against 128 registers at two blocks per SM).  Other sizes keep 128: on the 400-point
+// passes (320-thread blocks) 80 registers cost FWD_FIRST 24.5 -> 28.3 us and FWD_MID 17.3 -> 19.0
+// us.  The coil-summing INV_LAST runs 512-thread blocks and keeps 128 as well.
 template <int L1, int L2, PassKind KIND>
-__global__ void __maxnreg__(KIND == PASS_INV_LAST ? 128 : 80) k_line_fft2(LinePass a) {
+__global__ void __maxnreg__((KIND == PASS_INV_LAST || L2 != 32) ? 128 : 80) k_line_fft2(LinePass a) {
     pdl_wait();
     constexpr int DIR = (KIND == PASS_FWD_FIRST || KIND == PASS_FWD_MID) ? -1 : 1;
     constexpr int L = L1 * L2;

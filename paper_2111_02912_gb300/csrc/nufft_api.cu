@@ -475,7 +475,7 @@ struct Tile {
 Tile pick_tile(int L, int64_t B, int64_t S, bool coil_sum, int n_out) {
     Tile t{};
     if (fft2_factor(L, t.L1, t.L2)) {
-        // 8 adjacent lines (64-byte segments along the channel axis), three blocks per SM:
+        // 8 adjacent lines (64-byte segments along the channel axis), two or three blocks per SM:
         // measured faster than 4 or 16 lines on the 640-point passes.  The coil-summing last
         // inverse pass takes up to 16 coils per block, so 16 coils need no partial-sum pass.
         int TL = (coil_sum && S > 8) ? 16 : 8;
