@@ -163,7 +163,3 @@ class KBNufft:
         g = np.fft.ifftn(G, axes=tuple(range(len(lead), len(lead) + self.D))) * Ktot
         x = g[(Ellipsis,) + np.ix_(*self.place)]
         return self._scale_image(x)
-
-    def interp_matrix_row_sums(self):
-        """Sum of the J^D weights of every sample (used by pins)."""
-        return sum(w for _, w in self._tap_iter())

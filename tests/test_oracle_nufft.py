@@ -1,12 +1,16 @@
 """Pins of the FP64 same-kernel NUFFT oracle (Appendix) against quadrature, the exact NUDFT and its error bound."""
+import json
 import math
+import os
 
 import numpy as np
 import pytest
 from scipy.special import roots_legendre
 
 from oracle.nudft import NUDFT, nudft_adjoint, nudft_forward, voxel_centres
-from oracle.nufft import KBNufft, grid_size, kb_beta, kb_fourier, kb_kernel
+from oracle.nufft import KBNufft, grid_size, kb_beta, kb_fourier, kb_kernel, kb_kernel_deriv
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 @pytest.mark.parametrize("J,sigma", [(6, 2.0), (5, 1.25), (4, 2.0)])
@@ -25,6 +29,29 @@ def test_kernel_shape():
     u = np.linspace(-2.9, 2.9, 41)
     k = kb_kernel(u, J, beta)
     assert np.allclose(k, k[::-1]) and np.argmax(k) == 20                              # even, peak at 0
+
+
+def test_beta_matches_hand_evaluated_values():
+    """Beatty's beta at the paper's settings (Sec. IV-C), evaluated by hand in the golden file."""
+    gold = json.load(open(os.path.join(GOLDEN, "kb_beta_hand.json")))
+    for c in gold["cases"]:
+        assert math.isclose(kb_beta(c["J"], c["sigma"]), c["beta"], rel_tol=1e-9)
+
+
+@pytest.mark.parametrize("J,sigma", [(6, 2.0), (5, 1.25), (8, 2.0)])
+def test_kernel_derivative_matches_central_differences(J, sigma):
+    """d psi / du (used by the analytic-derivative autodiff variant of Sec. IV-A) against central
+    differences of psi itself, inside the support and away from its edges; odd symmetry; zero outside."""
+    beta = kb_beta(J, sigma)
+    u = np.linspace(-0.49 * J, 0.49 * J, 97)
+    h = 1e-5
+    fd = (kb_kernel(u + h, J, beta) - kb_kernel(u - h, J, beta)) / (2 * h)
+    d = kb_kernel_deriv(u, J, beta)
+    scale = np.max(np.abs(d))
+    assert np.max(np.abs(d - fd)) < 1e-7 * scale
+    assert np.allclose(d, -d[::-1], rtol=0, atol=1e-12 * scale)
+    assert kb_kernel_deriv(np.array([0.0]), J, beta)[0] == 0.0
+    assert kb_kernel_deriv(np.array([J / 2.0, -J / 2.0, J]), J, beta).tolist() == [0.0, 0.0, 0.0]
 
 
 def test_grid_size_rule():
