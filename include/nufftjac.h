@@ -60,7 +60,8 @@ enum {
     NUFFT_ERR_UNSUPPORTED = -2, /* D not in {1,2,3}, odd N_d, J out of [4,8], grid too large */
     NUFFT_ERR_OOM = -3,         /* device allocation failed */
     NUFFT_ERR_CUDA = -4,        /* a CUDA runtime call or kernel launch failed */
-    NUFFT_ERR_TIMEOUT = -5      /* reserved: a bounded device wait gave up */
+    NUFFT_ERR_TIMEOUT = -5      /* reserved, never returned: no kernel of this library waits on
+                                   another kernel, a flag or another GPU */
 };
 
 /* Plan options.  Fields left 0 take the defaults noted. */
@@ -73,9 +74,23 @@ typedef struct {
     double beta;      /* Kaiser-Bessel shape (<= 0 -> Beatty et al.:
                          pi sqrt((J/sigma)^2 (sigma-1/2)^2 - 0.8)) */
     int max_coils;    /* largest C any call on this plan will pass, 1..128 (0 -> 1) */
-    int bin_size[3];  /* spread tile edge per dim (0 -> automatic) */
-    int reserved[4];
+    int bin_size[3];  /* spread tile edge per dim (0 -> automatic: 256, 16x16, 8x8x8) */
+    int deterministic; /* 1: every output is bitwise reproducible from call to call (the 2-D
+                          adjoint adds its terms in an order fixed by the sort); 0: fastest
+                          order (the adjoint then agrees to rounding between calls) */
+    int spread_variant; /* adjoint spread kernel: NUFFT_SPREAD_AUTO (0), _STRIPS, _TILES, _GENERAL */
+    int reserved[2];
 } nufft_opts;
+
+/* Adjoint spread kernels (nufft_opts.spread_variant), all computing the transpose of the
+ * interpolation (Sec. II-D); AUTO takes STRIPS where it applies, else TILES, else GENERAL.
+ *   STRIPS  2-D only: a warp owns NSL grid rows x 16 columns in registers (NSL = 32 / coils per
+ *           warp, from max_coils); needs column bins of 16 (the default) and a grid of at
+ *           least 16 + J - 1 columns and NSL + J - 1 rows.
+ *   TILES   2-D / 3-D: a block owns one bin tile in shared memory (row or cell owners).
+ *   GENERAL any D: shared-memory atomics on bin tiles.
+ * Asking for a variant that does not apply to the plan returns NUFFT_ERR_UNSUPPORTED. */
+enum { NUFFT_SPREAD_AUTO = 0, NUFFT_SPREAD_STRIPS = 1, NUFFT_SPREAD_TILES = 2, NUFFT_SPREAD_GENERAL = 3 };
 
 /* Fill *o with defaults for a D-dimensional image of size n[0..D-1]. */
 void nufft_default_opts(nufft_opts* o, int dim, const int64_t* n);
@@ -85,11 +100,15 @@ void nufft_default_opts(nufft_opts* o, int dim, const int64_t* n);
  * depend on omega only).  m may be 0.  *out receives the plan. */
 int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* omega, void* stream);
 
-/* New sample locations (every trajectory update).  m may differ from the plan's
- * current m; growing past the capacity reallocates (synchronising).  The call
- * copies omega into the plan on `stream` (the caller's buffer is free once that
- * copy has run); the bin sort itself runs in the next call that needs the
- * points, on the plan's own stream, beside that call's FFT passes. */
+/* New sample locations (every trajectory update).  The Appendix's interpolation
+ * offsets k_m and coefficients u_j(omega_m) depend on omega only, so this is where
+ * they are fixed: the bin sort computes each point's window start and its D*J
+ * kernel weights once, and every later gather and spread of these points reads
+ * them.  m may differ from the plan's current m; growing past the capacity
+ * reallocates (synchronising).  The call copies omega into the plan on `stream`
+ * (the caller's buffer is free once that copy has run); the bin sort itself runs
+ * in the next call that needs the points, on the plan's own stream, beside that
+ * call's FFT passes. */
 int nufft_set_points(nufft_plan_t p, int64_t m, const float* omega, void* stream);
 
 /* y[C][M] = E x: forward NUFFT of each coil image (Sec. II-B, II-G). */
@@ -114,8 +133,9 @@ int nufft_jvp_omega(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cf
 int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cfloat* smaps,
                       const nufft_cfloat* v, float* grad_omega, nufft_cfloat* grad_x, void* stream);
 
-/* Device bytes a plan with these options and m points would allocate. */
-size_t nufft_workspace_bytes(const nufft_opts* o, int64_t m);
+/* Device bytes a plan with these options, m points and calls of up to C coils would allocate
+ * (C <= 0: o->max_coils).  Returns 0 for options nufft_plan would reject. */
+size_t nufft_workspace_bytes(const nufft_opts* o, int64_t m, int C);
 
 /* Plan facts for callers and benchmarks. */
 typedef struct {

@@ -16,6 +16,9 @@ NUFFT_ERR_OOM = -3
 NUFFT_ERR_CUDA = -4
 NUFFT_ERR_TIMEOUT = -5
 
+NUFFT_SPREAD_AUTO, NUFFT_SPREAD_STRIPS, NUFFT_SPREAD_TILES, NUFFT_SPREAD_GENERAL = 0, 1, 2, 3
+SPREAD_VARIANTS = {"auto": 0, "strips": 1, "tiles": 2, "general": 3}
+
 EXPORTED = (
     "nufft_default_opts", "nufft_plan", "nufft_set_points", "nufft_forward", "nufft_adjoint",
     "nufft_jvp_omega", "nufft_vjp_omega_x", "nufft_workspace_bytes", "nufft_get_info", "nufft_destroy",
@@ -29,7 +32,8 @@ NUFFT_NOALLOC_SCRATCH_BYTES = 32 << 20
 class nufft_opts(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("sigma", ctypes.c_double),
                 ("J", ctypes.c_int), ("beta", ctypes.c_double), ("max_coils", ctypes.c_int),
-                ("bin_size", ctypes.c_int * 3), ("reserved", ctypes.c_int * 4)]
+                ("bin_size", ctypes.c_int * 3), ("deterministic", ctypes.c_int), ("spread_variant", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class nufft_plan_info(ctypes.Structure):
@@ -67,7 +71,7 @@ def lib():
         L.nufft_vjp_omega_x.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
         L.nufft_forward_noalloc.argtypes = [ctypes.POINTER(nufft_opts), i64, vp, i32, vp, vp, vp, vp]
         L.nufft_forward_noalloc.restype = i32
-        L.nufft_workspace_bytes.argtypes = [ctypes.POINTER(nufft_opts), i64]
+        L.nufft_workspace_bytes.argtypes = [ctypes.POINTER(nufft_opts), i64, i32]
         L.nufft_workspace_bytes.restype = ctypes.c_size_t
         L.nufft_get_info.argtypes = [vp, ctypes.POINTER(nufft_plan_info)]
         L.nufft_destroy.argtypes = [vp]
@@ -132,8 +136,8 @@ def nufft_vjp_omega_x(plan, C, x, smaps, v, grad_omega, grad_x, stream=0):
     _check(lib().nufft_vjp_omega_x(plan, int(C), x, smaps, v, grad_omega, grad_x, stream), "nufft_vjp_omega_x")
 
 
-def nufft_workspace_bytes(opts, m):
-    return int(lib().nufft_workspace_bytes(ctypes.byref(opts), int(m)))
+def nufft_workspace_bytes(opts, m, C=0):
+    return int(lib().nufft_workspace_bytes(ctypes.byref(opts), int(m), int(C)))
 
 
 def nufft_get_info(plan):

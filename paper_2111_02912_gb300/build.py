@@ -12,7 +12,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libnufftjac.so")
 SOURCES = ["kernels_fft2_fwd_mid.cu", "kernels_fft2_fwd_first.cu", "kernels_fft2_inv_mid.cu", "kernels_fft2_inv_last.cu",
            "kernels_gather_d3.cu", "kernels_gather_d2.cu", "kernels_gather_d1.cu", "nufft_api.cu", "kernels_sort.cu",
-           "kernels_fft.cu", "kernels_spread.cu"]
+           "kernels_fft.cu", "kernels_spread.cu", "kernels_strip.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--extended-lambda",
          "-Xcompiler", "-Wall", "-diag-suppress", "177"]

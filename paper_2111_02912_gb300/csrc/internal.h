@@ -12,6 +12,67 @@ namespace nj {
 // start; each bin is a contiguous range.
 constexpr int kNbrStride = 64;        // entries per tile in tile_nbr: n, then 27 (start, prefix) pairs, total
 
+// ------------------------------------------------------ 2-D strip geometry
+// The 2-D adjoint spread runs on strip units: NSL consecutive grid rows by kStripW
+// consecutive columns (all coils of a coil group).  Unit u covers rows
+// R = (u / nb1) NSL .. R + NSL - 1 and columns (u % nb1) kStripW .. + kStripW - 1.
+constexpr int kStripW = 16;           // columns of a strip unit (the accumulators of one lane)
+struct StripGeom {
+    int K0, K1, nb1, J, NSL, ngroups;
+};
+
+// Strip units reached by the window starting at (k0, k1): the row groups (of NSL rows) holding
+// its J rows (mod K0) times the column tiles (of kStripW columns) holding its J columns (mod K1),
+// at most 5 x 3.  Calls unit(u, sd, dr) once per unit, with the window's start column relative to
+// the unit, sd in [-(J-1), kStripW), and its start-row offset R - k0 in [-(NSL-1), J-1].
+template <typename F>
+__device__ __forceinline__ void strip_point_units(const StripGeom& g, int k0, int k1, F unit) {
+    int tiles[3], sds[3], nt = 0;
+    for (int j = 0; j < g.J; ++j) {
+        int col = k1 + j;
+        if (col >= g.K1) col -= g.K1;
+        const int t = col / kStripW;
+        if (nt == 0 || t != tiles[nt - 1]) {
+            if (nt < 3) {
+                tiles[nt] = t;
+                sds[nt] = k1 - t * kStripW - (col < k1 ? g.K1 : 0);   // past the wrap: start lies left
+            }
+            ++nt;
+        }
+    }
+    int prev = -1;
+    for (int j = 0; j < g.J; ++j) {
+        int row = k0 + j;
+        if (row >= g.K0) row -= g.K0;
+        const int grp = row / g.NSL;
+        if (grp == prev) continue;
+        prev = grp;
+        const int dr = grp * g.NSL - k0 + (row < k0 ? g.K0 : 0);
+        for (int q = 0; q < nt && q < 3; ++q) unit(grp * g.nb1 + tiles[q], sds[q], dr);
+    }
+}
+
+// Sort-time tables of the strip spread (once per omega, read by every adjoint of those points).
+// A hit is a point whose window reaches a unit: {sorted point index, packed window start}, the
+// start column relative to the unit in bits 0..7 (biased by 8) and the start-row offset R - k0 in
+// bits 8..15 (biased by 32).  The hits of unit u are hits[hoff[u] .. hoff[u + 1]).  Work items are
+// {unit, first hit, end hit, split index} (split index -1: the unit is one item; else
+// splits[split index] = {part, parts, first partial slot, 0}); the parts of split units come first.
+struct StripTables {
+    int* hcount;      // [nunits]   hits per unit (counted by the scatter; zeroed before it)
+    int* hcur;        // [nunits]   fill cursors (zeroed by the plan)
+    int* hoff;        // [nunits+1] first hit of each unit
+    int2* hits;       // [hit_cap]
+    int64_t hit_cap;
+    int4* items;      // [nunits + slots]
+    int4* splits;     // [slots]
+    int* nitems;      // [0] items, [1] hits per part
+    int P;            // hits per part (doubled until the split parts fit the slots), a power of two
+    int slots;        // partial-sum slots
+    int* work;        // [2 per coil group] spread work counter and warps finished, zero between calls
+    int* partial_sums;  // [plan blocks][plan values] per-block totals of the plan
+};
+
 struct SortArgs {
     const float* omega;   // [D][M]
     int64_t m;
@@ -33,9 +94,13 @@ struct SortArgs {
     int* nitems;      // [1]
     int4* pidx;       // [M]
     float4* pfrac;    // [M]
-    float* pw;        // [M][ws]   kernel weights psi(u0_d - j) of the sorted points
-    int ws;
+    float* pw;        // [M][ws]   kernel weights psi(u0_d - j) of the sorted points, at d * wd + j
+    int ws, wd;
     KbPoly kb;
+    // 2-D strip mode: the scatter also counts the strip units' hits, then the plan and fill
+    int strip, nunits;
+    StripGeom sg;
+    StripTables st;
 };
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
 cudaError_t launch_key_count(const SortArgs& a, cudaStream_t s);     // histogram of bins, rank within bin
@@ -45,6 +110,11 @@ cudaError_t launch_item_scan(const SortArgs& a, cudaStream_t s);     // item off
 constexpr int kFusedTablesMaxBins = 8192;
 cudaError_t launch_sort_tables(const SortArgs& a, cudaStream_t s);   // the three above in one block
 cudaError_t launch_bin_scatter(const SortArgs& a, cudaStream_t s);   // records and weights in bin order
+// 2-D strip tables (kernels_strip.cu), after the scatter (which counts the hits per unit):
+cudaError_t launch_strip_plan(const SortArgs& a, int step, cudaStream_t s);   // step 0: block totals; 1: offsets, items
+int strip_plan_blocks(int nunits);   // blocks of the plan launches
+int strip_plan_vals();               // per-block totals the plan keeps
+cudaError_t launch_strip_fill(const SortArgs& a, cudaStream_t s);    // hit lists
 
 // Bins whose points can reach tile `bin` (tiles are the bins).  A window
 // covers J cells to the right of its start, so along each axis these are the
@@ -178,6 +248,7 @@ struct GatherArgs {
     const float2* v;      // [C][M]
     float* grad;          // [D][M]
     float2* v_sorted;     // VJP: if set, v is also written here in sorted point order, [C][M]
+    int v_sorted_cpt;     // ... in the strip layout [C / cpt][M][cpt] instead, when > 0
 };
 cudaError_t launch_gather_d1(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);
 cudaError_t launch_gather_d2(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);
@@ -209,6 +280,22 @@ struct SpreadArgs {
     KbPoly kb;
     float2* grid;         // [K...][C]
 };
+// 2-D strip spread (kernels_strip.cu): one warp per work item (a strip unit or a part of one).
+struct StripArgs {
+    PointsView pts;
+    StripGeom g;
+    StripTables t;
+    int max_items;
+    const float2* y;      // sorted coil values, [ncg][M][CPT] (coil c: group c / CPT, slot c % CPT)
+    int C, ncg;           // coils, coil groups of CPT = 32 / NSL coils
+    float2* grid;         // [K0][K1][C]
+    float2* partial;      // [slots][ncg][kStripW][32]
+    int* counters;        // [slots][ncg], zero between calls
+};
+cudaError_t launch_spread_strips(const StripArgs& a, cudaStream_t s);
+// ys = y[c][idx[i].w] in sorted point order, in the strip layout [ncg][M][cpt].
+cudaError_t launch_permute_y_strips(const int4* idx, const float2* y, float2* ys, int64_t M, int C, int cpt,
+                                    cudaStream_t s);
 cudaError_t launch_spread(const SpreadArgs& a, int cpl, cudaStream_t s, size_t smem);
 cudaError_t launch_zero_heavy_tiles(const SpreadArgs& a, cudaStream_t s);
 // ys[c][i] = y[c][idx[i].w]: the coil values in sorted point order (coalesced reads in the spread).

@@ -17,10 +17,13 @@
 namespace nj {
 
 // Weights of one sample into w[d * J + j] (shared, per group), copied from the
-// sort's per-point weights: lane q of the group loads q, q + G, ...
+// sort's per-point weights (at d * wd + j): lane q of the group loads q, q + G, ...
 template <int D, int J>
-__device__ __forceinline__ void group_weights(float* w, const float* pw, int lane_g, int G) {
-    for (int q = lane_g; q < D * J; q += G) w[q] = __ldg(pw + q);
+__device__ __forceinline__ void group_weights(float* w, const float* pw, int wd, int lane_g, int G) {
+    for (int q = lane_g; q < D * J; q += G) {
+        const int d = q / J;
+        w[q] = __ldg(pw + d * wd + (q - d * J));
+    }
 }
 
 // PAIR: lane l owns the coil pairs (2 (l + k G), 2 (l + k G) + 1), read as one 16-byte load
@@ -40,7 +43,7 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a) {
     int4 ix = make_int4(0, 0, 0, 0);
     if (valid) {
         ix = a.pts.idx[pt];
-        group_weights<D, J>(w, a.pts.w + pt * a.pts.ws, lane_g, G);
+        group_weights<D, J>(w, a.pts.w + pt * a.pts.ws, a.pts.wd, lane_g, G);
     }
     __syncwarp();
     if (!valid) return;
@@ -170,7 +173,14 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a) {
             for (int i = 0; i < W; ++i) {
                 const int64_t cv = W * (lane_g + k * G) + i;
                 const float2 v = __ldg(a.v + cv * M + orig);
-                if (a.v_sorted) a.v_sorted[cv * M + pt] = v;   // for the adjoint spread of the same v
+                if (a.v_sorted) {   // for the adjoint spread of the same v
+                    if (a.v_sorted_cpt) {
+                        const int64_t cg = cv / a.v_sorted_cpt;
+                        a.v_sorted[(cg * M + pt) * a.v_sorted_cpt + (cv - cg * a.v_sorted_cpt)] = v;
+                    } else {
+                        a.v_sorted[cv * M + pt] = v;
+                    }
+                }
 #pragma unroll
                 for (int d = 0; d < D; ++d) {
                     const float2 g = acc[d][k][i];

@@ -1,0 +1,471 @@
+// 2-D adjoint interpolation (spread), Sec. II-D: G[k] = sum_i psi(t_i - k) y_i,
+// the transpose of the gather, onto the oversampled grid [K0][K1][C], on strip units.
+//
+// A strip unit is NSL grid rows x kStripW columns.  A warp owns one unit (or one
+// part of a unit) for a coil group of CPT = 32 / NSL coils: lane (s, c) holds row
+// R + s, coil c of the group, all kStripW columns, in registers.
+//
+// Sort time (once per omega, read by every adjoint of the same points).  The
+// scatter counts every point as a hit of each unit its window reaches
+// (strip_point_units); the plan turns the counts into hit offsets and work items (a
+// unit with more than P hits is split into parts of P hits, and the parts of split
+// units are listed first, so they start in the first wave); the fill has every
+// point append {sorted point, packed window start} to the hit lists of its units.
+//
+// Spread.  Persistent blocks own every gridDim.x-th work item and their warps take
+// them in turn from a shared counter, loading the next item's descriptor and hit
+// records while the current one is processed.  A warp takes its item's hits 32 at
+// a time: each lane copies
+// one hit's kernel weights and CPT coil values into the warp's shared staging area
+// with asynchronous copies (cp.async), and then every hit is added to the accumulators
+// of all lanes at once: the lane's row tap comes from its row slot, and the column
+// taps land on compile-time register indices through a warp-uniform jump table on
+// the window's start column (strip_cases.inc, generated by gen_strip_cases.py).
+// There is no shared-memory read-modify-write and no block barrier.
+//
+// Each grid cell belongs to exactly one unit, whose owner writes it (zeros
+// included), so the grid needs no clearing and no atomics.  The parts of a split
+// unit store their partial sums in their own slots and count themselves done on
+// the unit's counter; the part that finishes last adds all the slots in part order
+// and writes the cells (no part ever waits), then resets the counter for the next
+// call.  Hits are summed in hit-list order and parts in part order, so the result
+// depends on the sort's order of the points only.
+#include <algorithm>
+#include <atomic>
+
+#include "internal.h"
+#include "strip_cases.inc"
+
+namespace nj {
+
+constexpr int kStripWarps = 4;
+constexpr int kStripBatch = 32;
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ int warp_inclusive_scan(int x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += v;
+    }
+    return x;
+}
+
+// Exclusive scan of V values per element over n elements, 1024 threads: tiles of 8192 elements,
+// warp w of a tile takes 256 consecutive elements as 8 rows of 32 (coalesced loads, shuffle scans).
+// get(i, v) loads element i (v[q] = 0 past n); put(i, excl, v) receives its exclusive prefixes.
+template <int V, typename Get, typename Put>
+__device__ __forceinline__ void block_scan_tiles(int n, int (&carry)[V], Get get, Put put) {
+    __shared__ int sh[V][32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int base = 0; base < n; base += 8192) {
+        int v[8][V], incl[8][V], run[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) run[q] = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = base + w * 256 + k * 32 + lane;
+            get(i, v[k]);
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const int x = warp_inclusive_scan(v[k][q], lane);
+                incl[k][q] = x + run[q];
+                run[q] += __shfl_sync(0xffffffffu, x, 31);
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < V; ++q) sh[q][w] = run[q];
+        }
+        __syncthreads();
+        int woff[V], tot[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int x = warp_inclusive_scan(sh[q][lane], lane);
+            woff[q] = __shfl_sync(0xffffffffu, x, w) - sh[q][w];
+            tot[q] = __shfl_sync(0xffffffffu, x, 31);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = base + w * 256 + k * 32 + lane;
+            int ex[V];
+#pragma unroll
+            for (int q = 0; q < V; ++q) ex[q] = carry[q] + woff[q] + incl[k][q] - v[k][q];
+            if (i < n) put(i, ex, v[k]);
+        }
+#pragma unroll
+        for (int q = 0; q < V; ++q) carry[q] += tot[q];
+        __syncthreads();   // sh is refilled by the next tile
+    }
+}
+
+// --------------------------------------------------------------- sort tables
+// Packed window start of a hit: column sd in [-(J-1), 15] and start-row offset dr in [-(NSL-1), J-1].
+__device__ __forceinline__ int strip_meta(int sd, int dr) { return (sd + 8) | ((dr + 32) << 8); }
+
+// The plan in two launches of 256-thread blocks (unit b * 256 + t in block b, thread t).  Split
+// parts are counted for P * 2^L, L = 0..7: the smallest level whose split parts fit the partial
+// slots is used.  (a) Per block and level: hits, split parts and whole units.  (b) Every block sums
+// the totals of the blocks before it, picks the level, scans its own units and writes their hit
+// offsets and items (split parts first: they start in the first wave), clearing the hit counts
+// (the next sort's scatter counts into them) and the fill cursors.
+constexpr int kPlanThreads = 256;
+constexpr int kPlanLevels = 8;
+constexpr int kPlanVals = 1 + 2 * kPlanLevels;   // hits, then split parts and whole units per level
+
+__device__ __forceinline__ int plan_parts(int h, int lgP) { return max(1, (int)(((int64_t)h + (1 << lgP) - 1) >> lgP)); }
+
+__global__ void __launch_bounds__(kPlanThreads) k_strip_plan_a(SortArgs a) {
+    pdl_wait();
+    __shared__ int sh[kPlanVals][kPlanThreads / 32];
+    const StripTables& T = a.st;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int u = blockIdx.x * kPlanThreads + t;
+    const int h = u < a.nunits ? T.hcount[u] : 0;
+    const int lgP = 31 - __clz(T.P);
+    int v[kPlanVals];
+    v[0] = h;
+#pragma unroll
+    for (int L = 0; L < kPlanLevels; ++L) {
+        const int parts = plan_parts(h, lgP + L);
+        v[1 + 2 * L] = u < a.nunits && parts > 1 ? parts : 0;
+        v[2 + 2 * L] = u < a.nunits && parts == 1 ? 1 : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < kPlanVals; ++q) {
+        int x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[q][w] = x;
+    }
+    __syncthreads();
+    if (t < kPlanVals) {
+        int x = 0;
+        for (int k = 0; k < kPlanThreads / 32; ++k) x += sh[t][k];
+        T.partial_sums[blockIdx.x * kPlanVals + t] = x;
+    }
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_strip_plan_b(SortArgs a) {
+    pdl_wait();
+    __shared__ int s_tot[kPlanVals], s_pre[kPlanVals];
+    __shared__ int sh[3][kPlanThreads / 32];
+    const StripTables& T = a.st;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int nblk = (int)gridDim.x, b = blockIdx.x;
+    if (t < kPlanVals) {
+        int tot = 0, pre = 0;
+        for (int k = 0; k < nblk; ++k) {
+            const int x = T.partial_sums[k * kPlanVals + t];
+            tot += x;
+            if (k < b) pre += x;
+        }
+        s_tot[t] = tot;
+        s_pre[t] = pre;
+    }
+    __syncthreads();
+    int L = 0;
+    while (L < kPlanLevels - 1 && s_tot[1 + 2 * L] > T.slots) ++L;
+    const bool fits = s_tot[1 + 2 * L] <= T.slots;
+    const int lgP = (31 - __clz(T.P)) + L;
+    const int H = fits ? s_tot[1 + 2 * L] : 0;   // split parts (items of split units come first)
+    const int u = b * kPlanThreads + t;
+    const bool live = u < a.nunits;
+    const int h = live ? T.hcount[u] : 0;
+    const int parts = fits ? plan_parts(h, lgP) : 1;
+    int v[3] = {h, live && parts > 1 ? parts : 0, live && parts == 1 ? 1 : 0};
+    int incl[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        int x = v[q];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        incl[q] = x;
+        if (lane == 31) sh[q][w] = x;
+    }
+    __syncthreads();
+    // prefixes of the blocks before this one (with no split anywhere every unit is one item, and
+    // the blocks before hold kPlanThreads units each)
+    const int base[3] = {s_pre[0], fits ? s_pre[1 + 2 * L] : 0, fits ? H + s_pre[2 + 2 * L] : b * kPlanThreads};
+    int ex[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        int wo = 0;
+        for (int k = 0; k < w; ++k) wo += sh[q][k];
+        ex[q] = base[q] + wo + incl[q] - v[q];
+    }
+    if (live) {
+        T.hoff[u] = ex[0];
+        T.hcount[u] = 0;
+        T.hcur[u] = 0;
+        if (v[1] > 0) {
+            for (int k = 0; k < parts; ++k) {
+                const int hb = ex[0] + (k << lgP);
+                T.items[ex[1] + k] = make_int4(u, hb, min(hb + (1 << lgP), ex[0] + h), ex[1] + k);
+                T.splits[ex[1] + k] = make_int4(k, parts, ex[1], 0);
+            }
+        } else {
+            T.items[ex[2]] = make_int4(u, ex[0], ex[0] + h, -1);
+        }
+    }
+    if (b == 0 && t == 0) {
+        T.hoff[a.nunits] = s_tot[0];
+        T.nitems[0] = fits ? H + s_tot[2 + 2 * L] : a.nunits;
+        T.nitems[1] = 1 << lgP;
+    }
+}
+
+// One thread per sorted point: the point joins the hit list of every unit its window reaches.
+__global__ void k_strip_fill(SortArgs a) {
+    pdl_wait();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.m) return;
+    const int4 ix = a.pidx[p];
+    const StripTables& T = a.st;
+    strip_point_units(a.sg, ix.x, ix.y, [&](int u, int sd, int dr) {
+        const int64_t pos = (int64_t)T.hoff[u] + atomicAdd(T.hcur + u, 1);
+        if (pos < T.hit_cap) T.hits[pos] = make_int2((int)p, strip_meta(sd, dr));
+    });
+}
+
+cudaError_t launch_strip_plan(const SortArgs& a, int step, cudaStream_t s) {
+    const unsigned nblk = (unsigned)((a.nunits + kPlanThreads - 1) / kPlanThreads);
+    if (step == 0) (void)launch_pdl(k_strip_plan_a, nblk, kPlanThreads, 0, s, a);
+    else (void)launch_pdl(k_strip_plan_b, nblk, kPlanThreads, 0, s, a);
+    return cudaGetLastError();
+}
+
+int strip_plan_blocks(int nunits) { return (nunits + kPlanThreads - 1) / kPlanThreads; }
+int strip_plan_vals() { return kPlanVals; }
+
+cudaError_t launch_strip_fill(const SortArgs& a, cudaStream_t s) {
+    if (a.m == 0) return cudaSuccess;
+    (void)launch_pdl(k_strip_fill, (unsigned)((a.m + 255) / 256), 256, 0, s, a);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------------- spread
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <int J, int NSL>
+__global__ void __launch_bounds__(kStripWarps * 32, 7) k_spread_strips(StripArgs a) {
+    pdl_wait();
+    constexpr int CPT = 32 / NSL;
+    // staging rows padded by 16 bytes, so that the 16-byte asynchronous copies of eight lanes fall on
+    // distinct banks: coil values 2 CPT + 2 floats (at least 4), weights 16 + 4 floats
+    constexpr int YP = (CPT < 2 ? 2 : CPT) + 2;   // in float2
+    constexpr int WP = 20;                        // in float: row taps [0, 8), column taps [8, 16)
+    __shared__ __align__(16) float2 s_y[kStripWarps][kStripBatch][YP];
+    __shared__ __align__(16) float s_w[kStripWarps][kStripBatch][WP];
+    __shared__ int2 s_m[kStripWarps][kStripBatch];   // {start column, start-row offset}
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cg = blockIdx.y;
+    const StripGeom g = a.g;
+    const int s = lane / CPT, c = lane - s * CPT;
+    const int coil = cg * CPT + c;
+    const int C = a.C;
+    const bool cok = coil < C;
+    const float2* yg = a.y + (int64_t)cg * a.pts.m * CPT;   // this coil group's values, [M][CPT]
+    const int nitems = a.t.nitems[0];
+    // Block b owns items b, b + gridDim.x, ... (split parts, first in the list, spread over the
+    // blocks); its warps take them in turn from a shared counter, so a warp that drew a heavy item
+    // takes fewer.  The next item's descriptor and first hit records are loaded while the current
+    // item is processed.
+    __shared__ int s_next;
+    if (threadIdx.x == 0) s_next = kStripWarps;
+    __syncthreads();   // the only block barrier: the counter is set before any warp takes from it
+    const int nb = (int)gridDim.x;
+    int it = (int)blockIdx.x + warp * nb;
+    int4 item = make_int4(0, 0, 0, -1);
+    int2 hit = make_int2(0, 0);
+    if (it < nitems) {
+        item = a.t.items[it];
+        if (lane < item.z - item.y) hit = a.t.hits[item.y + lane];
+    }
+    while (it < nitems) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(&s_next, 1);
+        const int itn = (int)blockIdx.x + __shfl_sync(0xffffffffu, k, 0) * nb;
+        int4 itemn = make_int4(0, 0, 0, -1);
+        if (itn < nitems) itemn = a.t.items[itn];
+        const int u = item.x;
+        const int grp = u / g.nb1, tc = u - grp * g.nb1;
+        const int R = grp * NSL, org1 = tc * kStripW;
+        const int NR = min(NSL, g.K0 - R);
+        const int Bt1 = min(kStripW, g.K1 - org1);
+
+        float acc[2 * kStripW];   // column k: real acc[2k], imaginary acc[2k + 1]
+#pragma unroll
+        for (int k = 0; k < 2 * kStripW; ++k) acc[k] = 0.f;
+        for (int b = item.y; b < item.z; b += kStripBatch) {
+            const int nh = min(kStripBatch, item.z - b);
+            if (b != item.y && lane < nh) hit = a.t.hits[b + lane];   // later batches of a split part
+            if (lane < nh) {
+                const float* pw = a.pts.w + (int64_t)hit.x * 16;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) cp_async16(&s_w[warp][lane][4 * q], pw + 4 * q);
+                const float2* py = yg + (int64_t)hit.x * CPT;
+                if constexpr (CPT >= 2) {
+#pragma unroll
+                    for (int q = 0; q < CPT / 2; ++q) cp_async16(&s_y[warp][lane][2 * q], py + 2 * q);
+                } else {
+                    cp_async8(&s_y[warp][lane][0], py);
+                }
+                s_m[warp][lane] = make_int2((hit.y & 255) - 8, (hit.y >> 8) - 32);
+            }
+            cp_async_wait_all();
+            __syncwarp();
+#pragma unroll 2
+            for (int h = 0; h < nh; ++h) {
+                const int2 m = s_m[warp][h];
+                const int ta = m.y + s;   // this lane's row tap
+                const float* w = s_w[warp][h];
+                const float wo = (unsigned)ta < (unsigned)J ? w[ta] : 0.f;
+                const float2 yv = s_y[warp][h][c];
+                const float4 wa = *(const float4*)(w + 8);
+                const float4 wb = *(const float4*)(w + 12);
+                const float wx[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+                strip_add_J<J>(acc, m.x, wx, wo * yv.x, wo * yv.y);
+            }
+            __syncwarp();   // the staging area is refilled by the next batch
+        }
+        // the next item's first hit records (its descriptor has arrived during the batches above)
+        int2 hitn = make_int2(0, 0);
+        if (itn < nitems && lane < itemn.z - itemn.y) hitn = a.t.hits[itemn.y + lane];
+
+        const bool rok = s < NR;
+        bool write = item.w < 0;
+        if (!write) {   // split unit: deposit this part, count it; the last part adds all parts in order
+            const int4 sp = a.t.splits[item.w];
+            const int part = sp.x, nparts = sp.y, slot0 = sp.z;
+            float2* pp = a.partial + ((int64_t)(slot0 + part) * a.ncg + cg) * (kStripW * 32);
+#pragma unroll
+            for (int k = 0; k < kStripW; ++k) pp[k * 32 + lane] = make_float2(acc[2 * k], acc[2 * k + 1]);
+            __threadfence();
+            __syncwarp();
+            int old = 0;
+            if (lane == 0) old = atomicAdd(a.counters + (int64_t)slot0 * a.ncg + cg, 1);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            if (old == nparts - 1) {
+                __threadfence();
+#pragma unroll
+                for (int k = 0; k < 2 * kStripW; ++k) acc[k] = 0.f;
+                for (int q2 = 0; q2 < nparts; ++q2) {
+                    const float2* src = a.partial + ((int64_t)(slot0 + q2) * a.ncg + cg) * (kStripW * 32);
+#pragma unroll
+                    for (int k = 0; k < kStripW; ++k) {
+                        const float2 v = __ldcg(src + k * 32 + lane);
+                        acc[2 * k] += v.x;
+                        acc[2 * k + 1] += v.y;
+                    }
+                }
+                if (lane == 0) a.counters[(int64_t)slot0 * a.ncg + cg] = 0;
+                write = true;
+            }
+        }
+        if (write && rok && cok) {
+            float2* dst = a.grid + ((int64_t)(R + s) * g.K1 + org1) * C + coil;
+#pragma unroll
+            for (int k = 0; k < kStripW; ++k)
+                if (k < Bt1) dst[(int64_t)k * C] = make_float2(acc[2 * k], acc[2 * k + 1]);
+        }
+        it = itn;
+        item = itemn;
+        hit = hitn;
+    }
+}
+
+// Resident blocks of a persistent kernel on the current device (queried once per kernel and device).
+template <auto KERNEL>
+static int resident_blocks(int threads) {
+    static std::atomic<int> n[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    int v = n[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, KERNEL, threads, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+        cudaGetLastError();
+        v = per_sm * sms;
+        n[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+template <int J, int NSL>
+static void strips_launch(const StripArgs& a, cudaStream_t s) {
+    constexpr int threads = kStripWarps * 32;
+    const int need = (a.max_items + kStripWarps - 1) / kStripWarps;
+    const int blocks = std::max(1, std::min(need, resident_blocks<k_spread_strips<J, NSL>>(threads)));
+    (void)launch_pdl(k_spread_strips<J, NSL>, dim3((unsigned)blocks, (unsigned)a.ncg), threads, 0, s, a);
+}
+
+template <int J>
+static cudaError_t strips_j(const StripArgs& a, cudaStream_t s) {
+    switch (a.g.NSL) {
+        case 2: strips_launch<J, 2>(a, s); break;
+        case 4: strips_launch<J, 4>(a, s); break;
+        case 8: strips_launch<J, 8>(a, s); break;
+        case 16: strips_launch<J, 16>(a, s); break;
+        default: strips_launch<J, 32>(a, s); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spread_strips(const StripArgs& a, cudaStream_t s) {
+    if (a.max_items == 0) return cudaSuccess;
+    switch (a.g.J) {
+        case 4: return strips_j<4>(a, s);
+        case 5: return strips_j<5>(a, s);
+        case 6: return strips_j<6>(a, s);
+        case 7: return strips_j<7>(a, s);
+        default: return strips_j<8>(a, s);
+    }
+}
+
+// Coil values in sorted point order, in the strip layout [C / cpt][M][cpt].
+__global__ void k_permute_y_strips(const int4* __restrict__ idx, const float2* __restrict__ y,
+                                   float2* __restrict__ ys, int64_t M, int C, int cpt) {
+    pdl_wait();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int64_t o = idx[i].w;
+    int c = 0;
+    for (; c + 4 <= C; c += 4) {   // four independent loads in flight
+        float2 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = __ldg(y + (int64_t)(c + k) * M + o);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int cc = c + k, grp = cc / cpt;
+            ys[((int64_t)grp * M + i) * cpt + (cc - grp * cpt)] = v[k];
+        }
+    }
+    for (; c < C; ++c) {
+        const int grp = c / cpt;
+        ys[((int64_t)grp * M + i) * cpt + (c - grp * cpt)] = __ldg(y + (int64_t)c * M + o);
+    }
+}
+
+cudaError_t launch_permute_y_strips(const int4* idx, const float2* y, float2* ys, int64_t M, int C, int cpt,
+                                    cudaStream_t s) {
+    if (M == 0) return cudaSuccess;
+    (void)launch_pdl(k_permute_y_strips, (unsigned)((M + 255) / 256), 256, 0, s, idx, y, ys, M, C, cpt);
+    return cudaGetLastError();
+}
+
+}  // namespace nj

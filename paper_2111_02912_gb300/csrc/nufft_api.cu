@@ -36,11 +36,13 @@ int fail(int status, const std::string& msg) {
 
 enum ProfKind {
     PK_ZERO, PK_BIN_COUNT, PK_BIN_SCAN, PK_TILE_SCAN, PK_BIN_SCATTER, PK_BIN_ITEMS, PK_FFT_FWD_FIRST, PK_FFT_FWD_MID,
-    PK_FFT_INV_MID, PK_FFT_INV_LAST, PK_GATHER_FWD, PK_GATHER_JVP, PK_GATHER_VJP, PK_ZERO_HEAVY, PK_SPREAD, PK_SUM_CHUNKS, PK_PERMUTE_Y, PK_COUNT
+    PK_FFT_INV_MID, PK_FFT_INV_LAST, PK_GATHER_FWD, PK_GATHER_JVP, PK_GATHER_VJP, PK_ZERO_HEAVY, PK_SPREAD, PK_SUM_CHUNKS, PK_PERMUTE_Y,
+    PK_STRIP_PLAN_A, PK_STRIP_PLAN_B, PK_STRIP_FILL, PK_COUNT
 };
 const char* kProfNames[PK_COUNT] = {"zero", "bin_count", "bin_scan", "tile_scan", "bin_scatter", "bin_items", "fft_fwd_first",
                                     "fft_fwd_mid", "fft_inv_mid", "fft_inv_last", "gather_fwd", "gather_jvp",
-                                    "gather_vjp", "zero_heavy", "spread", "sum_chunks", "permute_y"};
+                                    "gather_vjp", "zero_heavy", "spread", "sum_chunks", "permute_y",
+                                    "strip_plan_a", "strip_plan_b", "strip_fill"};
 
 int64_t grid_size(int64_t n, double sigma) {
     int64_t k = (int64_t)std::ceil(sigma * (double)n - 1e-9);
@@ -82,6 +84,20 @@ struct nufft_plan_s {
     // bins
     int B[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, nbins = 1, cpb = 1, P = 1024, CCmax = 1;
     bool cell_spread = false;   // spread by the row-owner tile kernel (else the general kernel)
+    // 2-D strip spread: sort keys (bin, start row), strip units of NSL rows x kStripW columns
+    bool strip = false;
+    int NSL = 2, nunits = 0, strip_P = 64, strip_slots = 0, ncg_max = 1;
+    float2* d_ys = nullptr;        // [ncg_max][M_cap][32 / NSL] coil values in sorted point order
+    float2* d_partial = nullptr;   // [strip_slots][ncg_max][kStripW][32]
+    int* d_counters = nullptr;     // [strip_slots][ncg_max], zero between calls
+    int* d_hcount = nullptr;       // [nunits] hits per strip unit
+    int* d_hcur = nullptr;         // [nunits] fill cursors
+    int* d_work = nullptr;         // [2 ncg_max] per coil group: spread work counter, warps finished
+    int* d_plan_sums = nullptr;    // per-block totals of the strip plan
+    int* d_hoff = nullptr;         // [nunits + 1]
+    int2* d_hits = nullptr;        // [hit_cap] strip hit lists
+    int64_t hit_cap = 0;
+    int4* d_splits = nullptr;      // [strip_slots]
     int* d_kcount = nullptr;
     bool kcount_clear = false;   // the bin histogram is known to be zero (the bin scan clears it)
     int* d_offsets = nullptr;
@@ -100,13 +116,15 @@ struct nufft_plan_s {
     // plan, beside that call's FFT passes (which do not need them); the call joins it before its
     // first kernel that reads the sorted points.  Fork and join stay inside one call.
     cudaStream_t aux = nullptr;
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr, join2_ev = nullptr;
     bool sort_pending = false;   // eager: omega copied by set_points, not yet sorted
     bool join_pending = false;   // sort launched on aux, not yet joined into a stream
+    bool join2_pending = false;  // strip plan and fill launched on aux after the join event, not yet joined
     bool cap_pending = false;    // the same for a set_points recorded into capture cap_id
     unsigned long long cap_id = 0;
     float* d_pw = nullptr;   // [M_cap][ws] kernel weights of the sorted points
-    int ws = 4;              // D*J rounded up to a multiple of 4
+    int ws = 4;              // D*J rounded up to a multiple of 4 (16 for the 2-D strips)
+    int wd = 6;              // weights per dimension in a row (J; 8 for the 2-D strips)
     float c_hi[3] = {0, 0, 0}, c_lo[3] = {0, 0, 0};
     // workspace
     float2* d_G = nullptr;
@@ -191,9 +209,12 @@ void free_plan(nufft_plan_s* p) {
     cudaFree(p->d_nitems); cudaFree(p->d_items); cudaFree(p->d_local); cudaFree(p->d_keyid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
     cudaFree(p->d_pw); cudaFree(p->d_om);
     cudaFree(p->d_G); cudaFree(p->d_T);
+    cudaFree(p->d_partial); cudaFree(p->d_counters); cudaFree(p->d_ys); cudaFree(p->d_hcount); cudaFree(p->d_hoff);
+    cudaFree(p->d_hits); cudaFree(p->d_splits); cudaFree(p->d_hcur); cudaFree(p->d_work); cudaFree(p->d_plan_sums);
     if (p->aux) cudaStreamDestroy(p->aux);
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     if (p->join_ev) cudaEventDestroy(p->join_ev);
+    if (p->join2_ev) cudaEventDestroy(p->join2_ev);
     for (auto& e : p->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto e : p->pool) cudaEventDestroy(e);
     delete p;
@@ -247,6 +268,31 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
     p.cell_spread = p.D >= 2 && tcells <= 512;
     for (int d = 0; d < p.D; ++d) p.cell_spread = p.cell_spread && p.B[d] + p.J - 1 <= p.K[d];
     p.P = p.cell_spread ? (int)tcells : (p.D == 3 ? 1024 : 512);
+    // 2-D strips: lanes are NSL row slots x 32 / NSL coils, the coils chosen from max_coils; a
+    // window must not reach a unit twice along either axis
+    {
+        const int cpt = p.maxC >= 9 ? 16 : (p.maxC >= 5 ? 8 : (p.maxC >= 3 ? 4 : (p.maxC == 2 ? 2 : 1)));
+        p.NSL = 32 / cpt;
+        p.ncg_max = (p.maxC + cpt - 1) / cpt;
+        // a window must not reach a unit twice: K1 >= 16 + J - 1 columns, K0 >= NSL + J - 1 rows
+        p.strip = p.D == 2 && p.K[1] >= kStripW + p.J - 1 && p.K[0] >= p.NSL + p.J - 1;
+        if (o->spread_variant == NUFFT_SPREAD_TILES || o->spread_variant == NUFFT_SPREAD_GENERAL) p.strip = false;
+        if (o->spread_variant == NUFFT_SPREAD_GENERAL) p.cell_spread = false;
+        if (o->spread_variant == NUFFT_SPREAD_STRIPS && !p.strip)
+            return fail(NUFFT_ERR_UNSUPPORTED, "strip spread needs D = 2, 16-cell column bins and a grid of at least "
+                                               "16 + J - 1 columns and 32 / coils + J - 1 rows");
+        if (o->spread_variant == NUFFT_SPREAD_TILES && !p.cell_spread)
+            return fail(NUFFT_ERR_UNSUPPORTED, "tile spread needs D >= 2, at most 512 cells per bin and bins of at "
+                                               "most K - J + 1 cells");
+        if (o->spread_variant < 0 || o->spread_variant > NUFFT_SPREAD_GENERAL)
+            return fail(NUFFT_ERR_INVALID_ARG, "unknown spread_variant");
+        if (p.strip) {
+            p.nunits = (int)(((p.K[0] + p.NSL - 1) / p.NSL) * ((p.K[1] + kStripW - 1) / kStripW));
+            // partial-sum slots for split units: ~nunits / 4, at most 16 MB (the sort lengthens the
+            // parts of split units when they would need more)
+            p.strip_slots = std::max(64, std::min(4096 / p.ncg_max, p.nunits / 4));
+        }
+    }
     // KB power-series coefficients a_k = (beta^2/4)^k / (k!)^2
     double ak = 1.0, sum = 0.0;
     const double q = p.beta * p.beta / 4.0;
@@ -257,7 +303,8 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
     }
     if (ak > 1e-9 * sum) return fail(NUFFT_ERR_UNSUPPORTED, "beta too large for the kernel power series");
     p.kb.two_over_j = (float)(2.0 / p.J);
-    p.ws = (p.D * p.J + 3) & ~3;
+    p.wd = p.strip ? 8 : p.J;   // the strip spread reads the column weights as two 16-byte loads
+    p.ws = p.strip ? 16 : (p.D * p.J + 3) & ~3;
     for (int d = 0; d < p.D; ++d) {
         const double c = (double)p.K[d] / (2.0 * M_PI);
         p.c_hi[d] = (float)c;
@@ -297,22 +344,51 @@ void workspace_elems(const nufft_plan_s& p, size_t& G, size_t& T) {
 size_t max_items(const nufft_plan_s& p, int64_t cap) {
     int nbr = 1;
     for (int d = 0; d < p.D; ++d) nbr *= std::min(3, p.nb[d]);
-    return (size_t)p.nbins + (size_t)((nbr * cap + p.P - 1) / p.P) + 1;
+    size_t n = (size_t)p.nbins + (size_t)((nbr * cap + p.P - 1) / p.P) + 1;
+    // strips: one item per unit, plus the extra parts of split units (at most the partial slots)
+    if (p.strip) n = std::max(n, (size_t)p.nunits + (size_t)p.strip_slots + 1);
+    return n;
 }
+
+// Sort histogram entries: bins, or (bin, start row) keys for the 2-D strips.
+int64_t sort_keys(const nufft_plan_s& p) { return (int64_t)p.nbins; }
+
+size_t strip_bytes(const nufft_plan_s& p) {
+    if (!p.strip) return 0;
+    return (size_t)p.strip_slots * (p.ncg_max * (kStripW * 32 * sizeof(float2) + sizeof(int)) + sizeof(int4)) +
+           (size_t)(3 * p.nunits + 3) * sizeof(int);
+}
+
+// Strip units a point's window can reach: its J rows span at most ceil((J - 1) / NSL) + 1 row
+// groups, one more where they wrap past the shorter last group, and its J columns at most three
+// column tiles (two, and a narrow last one).
+int64_t strip_hits_per_point(const nufft_plan_s& p) { return 3 * ((p.J - 2) / p.NSL + 3); }
 
 size_t point_bytes(const nufft_plan_s& p, int64_t cap) {
     size_t b = (size_t)cap * (2 * sizeof(int) + sizeof(int4) + sizeof(float4) + (p.ws + p.D) * sizeof(float)) +
                max_items(p, cap) * sizeof(int4);
+    if (p.strip)
+        b += (size_t)cap * ((size_t)p.ncg_max * (32 / p.NSL) * sizeof(float2) + strip_hits_per_point(p) * sizeof(int2));
     return b;
 }
 
 int alloc_points(nufft_plan_s* p, int64_t cap) {
     cudaFree(p->d_items); cudaFree(p->d_local); cudaFree(p->d_keyid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
-    cudaFree(p->d_pw); cudaFree(p->d_om);
+    cudaFree(p->d_pw); cudaFree(p->d_om); cudaFree(p->d_ys); cudaFree(p->d_hits);
     p->d_items = nullptr; p->d_local = p->d_keyid = nullptr; p->d_pidx = nullptr; p->d_pfrac = nullptr;
     p->d_pw = nullptr;
     p->d_om = nullptr;
+    p->d_ys = nullptr;
+    p->d_hits = nullptr;
     const size_t c = (size_t)std::max<int64_t>(cap, 1);
+    if (p->strip) {
+        p->hit_cap = (int64_t)c * strip_hits_per_point(*p);
+        if (cudaMalloc(&p->d_ys, c * (size_t)p->ncg_max * (32 / p->NSL) * sizeof(float2)) != cudaSuccess ||
+            cudaMalloc(&p->d_hits, (size_t)p->hit_cap * sizeof(int2)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(NUFFT_ERR_OOM, "device allocation of the strip hit lists failed");
+        }
+    }
     if (cudaMalloc(&p->d_items, max_items(*p, cap) * sizeof(int4)) != cudaSuccess ||
         cudaMalloc(&p->d_local, c * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&p->d_keyid, c * sizeof(int)) != cudaSuccess ||
@@ -325,6 +401,34 @@ int alloc_points(nufft_plan_s* p, int64_t cap) {
     }
     p->M_cap = cap;
     return NUFFT_OK;
+}
+
+StripTables strip_tables(const nufft_plan_s& p) {
+    StripTables t{};
+    t.hcount = p.d_hcount;
+    t.hcur = p.d_hcur;
+    t.work = p.d_work;
+    t.partial_sums = p.d_plan_sums;
+    t.hoff = p.d_hoff;
+    t.hits = p.d_hits;
+    t.hit_cap = p.hit_cap;
+    t.items = p.d_items;
+    t.splits = p.d_splits;
+    t.nitems = p.d_nitems;
+    t.P = p.strip_P;
+    t.slots = p.strip_slots;
+    return t;
+}
+
+StripGeom strip_geom(const nufft_plan_s& p) {
+    StripGeom g{};
+    g.K0 = (int)p.K[0];
+    g.K1 = (int)p.K[1];
+    g.nb1 = (int)((p.K[1] + kStripW - 1) / kStripW);
+    g.J = p.J;
+    g.NSL = p.NSL;
+    g.ngroups = (int)((p.K[0] + p.NSL - 1) / p.NSL);
+    return g;
 }
 
 SortArgs sort_args(nufft_plan_s* p, const float* omega) {
@@ -356,7 +460,12 @@ SortArgs sort_args(nufft_plan_s* p, const float* omega) {
     a.pfrac = p->d_pfrac;
     a.pw = p->d_pw;
     a.ws = p->ws;
+    a.wd = p->wd;
     a.kb = p->kb;
+    a.strip = p->strip ? 1 : 0;
+    a.nunits = p->nunits;
+    a.sg = strip_geom(*p);
+    a.st = strip_tables(*p);
     return a;
 }
 
@@ -425,10 +534,15 @@ int sort_rest(nufft_plan_s* p, cudaStream_t s) {
     int st;
     // every scan leaves the histogram zero for the next sort; a fresh one, or one in a graph, is cleared
     if ((capturing || !p->kcount_clear) &&
-        (st = launch(p, PK_ZERO, ss, [&] { return launch_zero(p->d_kcount, sizeof(int) * p->nbins, ss); })))
+        (st = launch(p, PK_ZERO, ss, [&] { return launch_zero(p->d_kcount, sizeof(int) * sort_keys(*p), ss); })))
         return st;
     if ((st = launch(p, PK_BIN_COUNT, ss, [&] { return launch_key_count(a, ss); }))) return st;
-    if (p->nbins <= kFusedTablesMaxBins) {
+    if (p->strip && (capturing || !p->kcount_clear) &&
+        (st = launch(p, PK_ZERO, ss, [&] { return launch_zero(p->d_hcount, sizeof(int) * p->nunits, ss); })))
+        return st;
+    if (p->strip) {   // bin offsets only: the strip spread needs no tile lists
+        if ((st = launch(p, PK_BIN_SCAN, ss, [&] { return launch_bin_scan(a, ss); }))) return st;
+    } else if (p->nbins <= kFusedTablesMaxBins) {
         if ((st = launch(p, PK_BIN_SCAN, ss, [&] { return launch_sort_tables(a, ss); }))) return st;
     } else {
         if ((st = launch(p, PK_BIN_SCAN, ss, [&] { return launch_bin_scan(a, ss); }))) return st;
@@ -441,7 +555,37 @@ int sort_rest(nufft_plan_s* p, cudaStream_t s) {
         NJ_CUDA(cudaEventRecord(p->join_ev, p->aux));
         p->join_pending = true;
     }
+    // The strip tables (hit offsets, work items, hit lists) are needed by the adjoint spread only:
+    // they run behind the join event, beside the kernels that read the sorted points, and are
+    // joined before the spread or at the end of the call (strip_join).
+    if (p->strip) {
+        if ((st = launch(p, PK_STRIP_PLAN_A, ss, [&] { return launch_strip_plan(a, 0, ss); }))) return st;
+        if ((st = launch(p, PK_STRIP_PLAN_B, ss, [&] { return launch_strip_plan(a, 1, ss); }))) return st;
+        if ((st = launch(p, PK_STRIP_FILL, ss, [&] { return launch_strip_fill(a, ss); }))) return st;
+        if (p->aux) {
+            NJ_CUDA(cudaEventRecord(p->join2_ev, p->aux));
+            p->join2_pending = true;
+        }
+    }
     return NUFFT_OK;
+}
+
+int sort_join(nufft_plan_s* p, cudaStream_t s);
+
+// Makes s wait for the strip tables (before the strip spread, and at the end of every call that
+// started a sort, so that each call stays self-contained).
+int strip_join(nufft_plan_s* p, cudaStream_t s) {
+    if (!p->join2_pending) return NUFFT_OK;
+    p->join2_pending = false;
+    NJ_CUDA(cudaStreamWaitEvent(s, p->join2_ev, 0));
+    return NUFFT_OK;
+}
+
+// End of an entry point: every piece of the plan's second stream is joined into s.
+int finish_call(nufft_plan_s* p, cudaStream_t s, int st) {
+    if (st) return st;
+    if ((st = sort_join(p, s))) return st;
+    return strip_join(p, s);
 }
 
 // Makes s wait for the sort before a kernel that reads the sorted points.
@@ -570,15 +714,42 @@ int forward_grids(nufft_plan_s* p, int C, int nd, int has_plain, const float2* x
     return NUFFT_OK;
 }
 
+int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cudaStream_t s);
+
 // Adjoint of the interpolation + FFT + scaling for C coil channels of y.
 // ysorted: y already copied into T in sorted point order (by the VJP gather), else null.
 int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, float2* xout, cudaStream_t s,
                  const float2* ysorted = nullptr) {
     const int D = p->D;
     int st;
+    if (p->strip) {
+        // 2-D strips: every grid cell written once by its unit; y in sorted point-major order
+        StripArgs ta{};
+        ta.pts = PointsView{p->d_pidx, p->d_pfrac, p->M, p->d_pw, p->ws, p->wd};
+        ta.g = strip_geom(*p);
+        ta.t = strip_tables(*p);
+        ta.max_items = p->nunits + p->strip_slots;
+        ta.C = C;
+        const int cpt = 32 / p->NSL;
+        ta.ncg = (C + cpt - 1) / cpt;
+        ta.grid = p->d_G;
+        ta.partial = p->d_partial;
+        ta.counters = p->d_counters;
+        if (ysorted) {
+            ta.y = ysorted;
+        } else {
+            if ((st = launch(p, PK_PERMUTE_Y, s,
+                             [&] { return launch_permute_y_strips(p->d_pidx, y, p->d_ys, p->M, C, cpt, s); })))
+                return st;
+            ta.y = p->d_ys;
+        }
+        if ((st = strip_join(p, s))) return st;
+        if ((st = launch(p, PK_SPREAD, s, [&] { return launch_spread_strips(ta, s); }))) return st;
+        return inverse_passes(p, C, smaps, xout, s);
+    }
     // spread: output-driven tiles; only tiles split over several work items are cleared first
     SpreadArgs sa{};
-    sa.pts = PointsView{p->d_pidx, p->d_pfrac, p->M, p->d_pw, p->ws};
+    sa.pts = PointsView{p->d_pidx, p->d_pfrac, p->M, p->d_pw, p->ws, p->wd};
     sa.D = D;
     sa.J = p->J;
     for (int d = 0; d < 3; ++d) {
@@ -625,7 +796,14 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
     } else {
         if ((st = launch(p, PK_SPREAD, s, [&] { return launch_spread(sa, cpl, s, ssm); }))) return st;
     }
-    // inverse FFT passes, dim 0 first; the last one crops, scales and applies maps
+    return inverse_passes(p, C, smaps, xout, s);
+}
+
+// Inverse FFT passes over the spread grid in p->d_G, dim 0 first; the last one crops, scales and
+// applies the conjugate maps (summing the coils) or writes one image per coil.
+int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cudaStream_t s) {
+    const int D = p->D;
+    int st;
     const float2* in = p->d_G;
     ImageSide im = image_side(p, C, nullptr, smaps, xout, 0);
     for (int d = 0; d < D; ++d) {
@@ -681,7 +859,7 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
 
 GatherArgs gather_args(nufft_plan_s* p, int C, int nd, int has_plain) {
     GatherArgs g{};
-    g.pts = PointsView{p->d_pidx, p->d_pfrac, p->M, p->d_pw, p->ws};
+    g.pts = PointsView{p->d_pidx, p->d_pfrac, p->M, p->d_pw, p->ws, p->wd};
     g.D = p->D;
     g.J = p->J;
     for (int d = 0; d < 3; ++d) g.K[d] = (int)p->K[d];
@@ -724,13 +902,16 @@ void nufft_default_opts(nufft_opts* o, int dim, const int64_t* n) {
     o->max_coils = 1;
 }
 
-size_t nufft_workspace_bytes(const nufft_opts* o, int64_t m) {
+size_t nufft_workspace_bytes(const nufft_opts* o, int64_t m, int C) {
+    if (!o) return 0;
+    nufft_opts oc = *o;
+    if (C > 0) oc.max_coils = C;
     nufft_plan_s p;
-    if (validate_opts(o, p) != NUFFT_OK) return 0;
+    if (validate_opts(&oc, p) != NUFFT_OK) return 0;
     size_t G, T;
     workspace_elems(p, G, T);
     size_t b = (G + T) * sizeof(float2) + point_bytes(p, std::max<int64_t>(m, 1));
-    b += (size_t)((5 + kNbrStride) * p.nbins + 7) * sizeof(int);
+    b += (size_t)((4 + kNbrStride) * p.nbins + 2 * sort_keys(p) + 8) * sizeof(int) + strip_bytes(p);
     for (int d = 0; d < p.D; ++d) b += (size_t)p.N[d] * sizeof(float) + (size_t)p.K[d] * sizeof(float2);
     return b;
 }
@@ -765,15 +946,31 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
         build_fft_axis(L, p->axis[d]);
         p->axis[d].tw = p->d_tw[d];
     }
-    if (cudaMalloc(&p->d_kcount, sizeof(int) * p->nbins) != cudaSuccess ||
-        cudaMalloc(&p->d_offsets, sizeof(int) * (p->nbins + 1)) != cudaSuccess ||
+    if (cudaMalloc(&p->d_kcount, sizeof(int) * sort_keys(*p)) != cudaSuccess ||
+        cudaMalloc(&p->d_offsets, sizeof(int) * (sort_keys(*p) + 1)) != cudaSuccess ||
         cudaMalloc(&p->d_item_off, sizeof(int) * (p->nbins + 1)) != cudaSuccess ||
         cudaMalloc(&p->d_tile_parts, sizeof(int) * p->nbins) != cudaSuccess ||
         cudaMalloc(&p->d_heavy, sizeof(int) * (p->nbins + 1)) != cudaSuccess ||
         cudaMalloc(&p->d_tile_nbr, sizeof(int) * kNbrStride * p->nbins) != cudaSuccess ||
-        cudaMalloc(&p->d_nitems, sizeof(int)) != cudaSuccess)
+        cudaMalloc(&p->d_nitems, 2 * sizeof(int)) != cudaSuccess)
         return oom("bins");
-    cudaMemset(p->d_nitems, 0, sizeof(int));
+    cudaMemset(p->d_nitems, 0, 2 * sizeof(int));
+    if (p->strip) {
+        const size_t nslot = (size_t)p->strip_slots * p->ncg_max;
+        if (cudaMalloc(&p->d_partial, nslot * kStripW * 32 * sizeof(float2)) != cudaSuccess ||
+            cudaMalloc(&p->d_counters, nslot * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&p->d_hcount, (size_t)p->nunits * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&p->d_hcur, (size_t)p->nunits * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&p->d_work, 2 * (size_t)p->ncg_max * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&p->d_plan_sums, (size_t)strip_plan_blocks(p->nunits) * strip_plan_vals() * sizeof(int)) !=
+                cudaSuccess ||
+            cudaMalloc(&p->d_hoff, (size_t)(p->nunits + 1) * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&p->d_splits, (size_t)p->strip_slots * sizeof(int4)) != cudaSuccess)
+            return oom("strip partial sums");
+        cudaMemset(p->d_counters, 0, nslot * sizeof(int));
+        cudaMemset(p->d_hcount, 0, (size_t)p->nunits * sizeof(int));
+        cudaMemset(p->d_work, 0, 2 * (size_t)p->ncg_max * sizeof(int));
+    }
     workspace_elems(*p, p->G_elems, p->T_elems);
     if (cudaMalloc(&p->d_G, p->G_elems * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&p->d_T, p->T_elems * sizeof(float2)) != cudaSuccess)
@@ -786,7 +983,8 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
     }
     if (cudaStreamCreateWithPriority(&p->aux, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->join2_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         free_plan(p);
         return fail(NUFFT_ERR_CUDA, "stream or event creation failed");
@@ -810,13 +1008,13 @@ int nufft_forward(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cflo
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
     if ((st = sort_rest(p, s))) return st;
-    if (p->M == 0) return sort_join(p, s);
+    if (p->M == 0) return finish_call(p, s, NUFFT_OK);
     if ((st = forward_grids(p, C, 1, 1, (const float2*)x, (const float2*)smaps, s))) return st;
     if ((st = sort_join(p, s))) return st;
     GatherArgs g = gather_args(p, C, 1, 1);
     g.y = (float2*)y;
     const int cpl = gather_cpl(g);
-    return launch(p, PK_GATHER_FWD, s, [&] { return launch_gather(GM_FWD, g, cpl, s); });
+    return finish_call(p, s, launch(p, PK_GATHER_FWD, s, [&] { return launch_gather(GM_FWD, g, cpl, s); }));
 }
 
 int nufft_adjoint(nufft_plan_t p, int C, const nufft_cfloat* y, const nufft_cfloat* smaps, nufft_cfloat* x,
@@ -827,7 +1025,7 @@ int nufft_adjoint(nufft_plan_t p, int C, const nufft_cfloat* y, const nufft_cflo
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
     if ((st = sort_rest(p, s)) || (st = sort_join(p, s))) return st;
-    return adjoint_impl(p, C, (const float2*)y, (const float2*)smaps, (float2*)x, s);
+    return finish_call(p, s, adjoint_impl(p, C, (const float2*)y, (const float2*)smaps, (float2*)x, s));
 }
 
 int nufft_jvp_omega(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cfloat* smaps, const float* domega,
@@ -838,7 +1036,7 @@ int nufft_jvp_omega(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cf
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
     if ((st = sort_rest(p, s))) return st;
-    if (p->M == 0) return sort_join(p, s);
+    if (p->M == 0) return finish_call(p, s, NUFFT_OK);
     const int hp = y_or_null ? 1 : 0;
     const int nd = p->D + hp;
     if ((st = forward_grids(p, C, nd, hp, (const float2*)x, (const float2*)smaps, s))) return st;
@@ -848,7 +1046,7 @@ int nufft_jvp_omega(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cf
     g.dy = (float2*)dy;
     g.domega = domega;
     const int cpl = gather_cpl(g);
-    return launch(p, PK_GATHER_JVP, s, [&] { return launch_gather(GM_JVP, g, cpl, s); });
+    return finish_call(p, s, launch(p, PK_GATHER_JVP, s, [&] { return launch_gather(GM_JVP, g, cpl, s); }));
 }
 
 int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cfloat* smaps, const nufft_cfloat* v,
@@ -868,7 +1066,11 @@ int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_
         GatherArgs g = gather_args(p, C, p->D, 0);
         g.v = (const float2*)v;
         g.grad = grad_omega;
-        if (grad_x && p->cell_spread && (size_t)C * (size_t)p->M <= p->T_elems) {
+        if (grad_x && p->strip) {
+            g.v_sorted = p->d_ys;
+            g.v_sorted_cpt = 32 / p->NSL;
+            vsorted = p->d_ys;
+        } else if (grad_x && p->cell_spread && (size_t)C * (size_t)p->M <= p->T_elems) {
             g.v_sorted = p->d_T;
             vsorted = p->d_T;
         }
@@ -876,8 +1078,8 @@ int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_
         if ((st = launch(p, PK_GATHER_VJP, s, [&] { return launch_gather(GM_VJP, g, cpl, s); }))) return st;
     }
     if ((st = sort_join(p, s))) return st;
-    if (grad_x) return adjoint_impl(p, C, (const float2*)v, (const float2*)smaps, (float2*)grad_x, s, vsorted);
-    return NUFFT_OK;
+    if (grad_x) st = adjoint_impl(p, C, (const float2*)v, (const float2*)smaps, (float2*)grad_x, s, vsorted);
+    return finish_call(p, s, st);
 }
 
 int nufft_get_info(nufft_plan_t p, nufft_plan_info* info) {
@@ -895,7 +1097,7 @@ int nufft_get_info(nufft_plan_t p, nufft_plan_info* info) {
     info->m = p->M;
     info->nbins = p->nbins;
     info->max_coils = p->maxC;
-    info->workspace_bytes = (p->G_elems + p->T_elems) * sizeof(float2) + point_bytes(*p, p->M_cap);
+    info->workspace_bytes = (p->G_elems + p->T_elems) * sizeof(float2) + point_bytes(*p, p->M_cap) + strip_bytes(*p);
     return NUFFT_OK;
 }
 
@@ -1014,6 +1216,9 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
     nufft_plan_s p;   // host-side description only; every device pointer below is scratch
     int st = validate_opts(o, p);
     if (st) return st;
+    p.strip = false;   // forward only: the bin sort without the adjoint's strip tables
+    p.wd = p.J;
+    p.ws = (p.D * p.J + 3) & ~3;
     if (C < 1 || C > 128) return fail(NUFFT_ERR_INVALID_ARG, "C must lie in [1, 128]");
     if (m < 0 || m > (int64_t)INT32_MAX) return fail(NUFFT_ERR_INVALID_ARG, "m out of range");
     if (m > 0 && (!omega || !x || !y)) return fail(NUFFT_ERR_INVALID_ARG, "omega, x or y is NULL");

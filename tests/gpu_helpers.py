@@ -31,3 +31,10 @@ def to_dev(a):
 
 def host(t):
     return None if t is None else t.detach().cpu().numpy()
+
+
+def max_rel(a, b):
+    """Largest element error over the largest reference magnitude (catches a few wrong cells)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))

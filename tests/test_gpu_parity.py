@@ -6,7 +6,7 @@ exact NUDFT, 1e-3 for grad_omega against the exact Jacobian.
 import numpy as np
 import pytest
 
-from gpu_helpers import host, make_case, rel, to_dev
+from gpu_helpers import host, make_case, max_rel, rel, to_dev
 from oracle import jacobian as jb
 from oracle.nudft import NUDFT
 from oracle.nufft import KBNufft
@@ -87,13 +87,69 @@ def test_all_products_match_same_kernel_oracle(name, shape, M, C, maps, opts):
     y_ref = jb.sense_forward(op, case["x"], s)
     assert rel(host(y), y_ref) < TOL_SAME
     assert rel(host(y2), y_ref) < TOL_SAME
-    assert rel(host(xa), jb.sense_adjoint(op, case["y"], s)) < TOL_SAME
+    xa_ref = jb.sense_adjoint(op, case["y"], s)
+    assert rel(host(xa), xa_ref) < TOL_SAME
+    assert max_rel(host(xa), xa_ref) < TOL_SAME       # element by element, not only in the norm
     dy_ref = jb.jvp_omega(op, case["x"], case["domega"], s)
     assert rel(host(dy), dy_ref) < TOL_SAME
     assert rel(host(dy_only), dy_ref) < TOL_SAME
     go_ref, gx_ref = jb.vjp_omega_x(op, case["x"], case["v"], s)
     assert rel(host(go), go_ref) < TOL_SAME
     assert rel(host(gx), gx_ref) < TOL_SAME
+    assert max_rel(host(gx), gx_ref) < TOL_SAME
+
+
+# The 2-D strip spread: every coils-per-warp width (32 / NSL coils for NSL rows), J 4..8, grids
+# just wide enough for it (K1 = 16 + J - 1 columns, K0 = NSL + J - 1 rows: windows wrap around both
+# axes), several coil groups, and the two other spread kernels on the same problem.
+STRIP_CASES = [
+    # name, shape, M, C, maps, opts
+    ("strip_c1", (48, 40), 2500, 1, False, {}),
+    ("strip_c2", (40, 48), 2500, 2, True, {}),
+    ("strip_c3", (36, 20), 1500, 3, False, {}),
+    ("strip_c5", (24, 32), 1500, 5, True, {}),
+    ("strip_c12", (32, 24), 1200, 12, True, {}),
+    ("strip_c20_two_groups", (24, 40), 1500, 20, True, {}),
+    ("strip_c33_three_groups", (20, 24), 800, 33, True, {}),
+    ("strip_narrow_J4", (20, 10), 900, 4, True, dict(J=4)),          # K = 40 x 20, K1 = 16 + J
+    ("strip_narrow_J6", (12, 12), 600, 16, True, {}),                # K = 24 x 24: K1 = 16 + J + 2
+    ("strip_narrow_J8", (20, 12), 700, 2, True, dict(J=8)),          # K1 = 24 = 16 + J
+    ("strip_J5_odd_width", (30, 26), 1200, 6, True, dict(J=5)),
+    ("strip_J7_ragged_tile", (34, 22), 1100, 8, True, dict(J=7)),    # K1 = 44: last column tile 12 wide
+    ("strip_sigma125", (64, 48), 2000, 4, True, dict(sigma=1.25)),   # K = 80 x 60
+    ("strip_variant_tiles", (32, 40), 1500, 3, True, dict(spread="tiles")),
+    ("strip_variant_general", (32, 40), 1500, 3, True, dict(spread="general")),
+    ("strip_variant_strips", (32, 40), 1500, 3, True, dict(spread="strips")),
+]
+
+
+@pytest.mark.parametrize("name,shape,M,C,maps,opts", STRIP_CASES, ids=[c[0] for c in STRIP_CASES])
+def test_strip_spread_adjoint_and_vjp(name, shape, M, C, maps, opts):
+    import torch
+    seed = sum(map(ord, name))
+    case = make_case(shape, M, C, maps, seed=seed)
+    plan = _plan(case, **opts)
+    X, S, V, Y = (to_dev(case[k]) for k in ("x", "smaps", "v", "y"))
+    xa = plan.adjoint(Y, S)
+    go, gx = plan.vjp_omega_x(X, V, S)
+    gx_only = plan.vjp_omega_x(X, V, S, need_omega=False)[1]
+    torch.cuda.synchronize()
+    op = KBNufft(shape, case["omega"], **{k: v for k, v in opts.items() if k in ("J", "sigma")})
+    s = case["smaps"]
+    xa_ref = jb.sense_adjoint(op, case["y"], s)
+    assert rel(host(xa), xa_ref) < TOL_SAME and max_rel(host(xa), xa_ref) < TOL_SAME
+    go_ref, gx_ref = jb.vjp_omega_x(op, case["x"], case["v"], s)
+    assert rel(host(go), go_ref) < TOL_SAME
+    assert rel(host(gx), gx_ref) < TOL_SAME and max_rel(host(gx), gx_ref) < TOL_SAME
+    assert rel(host(gx_only), gx_ref) < TOL_SAME
+
+
+def test_strip_variant_refused_where_it_does_not_apply():
+    from paper_2111_02912_gb300 import _abi
+    case = make_case((8, 10), 100, 2, True, seed=1)            # K1 = 20 < 16 + J - 1
+    with pytest.raises(_abi.NufftError) as e:
+        _plan(case, spread="strips")
+    assert e.value.status == _abi.NUFFT_ERR_UNSUPPORTED
 
 
 def test_small64_against_exact_nudft_and_jacobian():
