@@ -2,12 +2,13 @@
 
 For a hit whose window starts at unit-relative column sd (-7 <= sd <= 15), tap j
 (0 <= j < J) of the window lands on column sd + j, and only the columns inside the
-unit [0, 16) are kept.  The kernel keeps the 16 columns of a lane in registers, so
-each start column needs its own instruction sequence with compile-time register
-operands; a warp-uniform brx.idx (index sd + 7) jumps to it.  Operands: %0..%31 the
-accumulators (column k: real %2k, imaginary %2k+1), %32 the case index, %33..%40
-the column weights w[0..7], %41/%42 the real/imaginary parts of the weighted coil
-value.  Run from this directory: python gen_strip_cases.py
+unit [0, 16) are kept.  The kernel keeps the 16 columns of a lane (two coils each)
+in registers, so each start column needs its own instruction sequence with
+compile-time register operands; a warp-uniform brx.idx (index sd + 7) jumps to it.
+Operands: %0..%63 the accumulators (column k: %4k..%4k+3 = real and imaginary parts
+of the lane's two coils), %64 the case index, %65..%72 the column weights w[0..7],
+%73..%76 the weighted coil values (real, imaginary of the first coil, then the
+second).  Run from this directory: python gen_strip_cases.py
 """
 import os
 
@@ -22,8 +23,8 @@ def case_lines(J):
         for j in range(J):
             col = sd + j
             if 0 <= col < W:
-                ins.append("fma.rn.f32 %%%d, %%%d, %%41, %%%d;" % (2 * col, 33 + j, 2 * col))
-                ins.append("fma.rn.f32 %%%d, %%%d, %%42, %%%d;" % (2 * col + 1, 33 + j, 2 * col + 1))
+                for q in range(4):
+                    ins.append("fma.rn.f32 %%%d, %%%d, %%%d, %%%d;" % (4 * col + q, 65 + j, 73 + q, 4 * col + q))
         ins.append("bra.uni SE;")
         out.append('        "S%d: %s\\n\\t"' % (sd - SD_MIN, " ".join(ins)))
     return out
@@ -33,21 +34,21 @@ def main():
     n = SD_MAX - SD_MIN + 1
     labels = ", ".join("S%d" % i for i in range(n))
     text = ["// Generated by gen_strip_cases.py (same directory); do not edit by hand.",
-            "// strip_add_J<J>(acc, sd, w, yw): acc[sd + j] += w[j] * yw for the taps j < J whose",
-            "// column sd + j lies in [0, 16); sd in [-7, 15] (warp-uniform).",
+            "// strip_add_J<J>(acc, sd, w, y): acc[4 (sd + j) + q] += w[j] * y[q] for the taps j < J",
+            "// whose column sd + j lies in [0, 16), q < 4; sd in [-7, 15] (warp-uniform).",
             "#pragma once", "", "namespace nj {", "",
             "template <int J>",
-            "__device__ __forceinline__ void strip_add_J(float (&a)[32], int sd, const float (&w)[8], float yx, float yy);",
+            "__device__ __forceinline__ void strip_add_J(float (&a)[64], int sd, const float (&w)[8], const float (&y)[4]);",
             ""]
-    outs = ", ".join('"+f"(a[%d])' % k for k in range(32))
-    ins = ", ".join(['"r"(sd + 7)'] + ['"f"(w[%d])' % j for j in range(8)] + ['"f"(yx)', '"f"(yy)'])
+    outs = ", ".join('"+f"(a[%d])' % k for k in range(64))
+    ins = ", ".join(['"r"(sd + 7)'] + ['"f"(w[%d])' % j for j in range(8)] + ['"f"(y[%d])' % q for q in range(4)])
     for J in range(4, 9):
         text.append("template <>")
-        text.append("__device__ __forceinline__ void strip_add_J<%d>(float (&a)[32], int sd, const float (&w)[8], "
-                    "float yx, float yy) {" % J)
+        text.append("__device__ __forceinline__ void strip_add_J<%d>(float (&a)[64], int sd, const float (&w)[8], "
+                    "const float (&y)[4]) {" % J)
         text.append('    asm volatile("{\\n\\t"')
         text.append('        "st: .branchtargets %s;\\n\\t"' % labels)
-        text.append('        "brx.idx.uni %32, st;\\n\\t"')
+        text.append('        "brx.idx.uni %64, st;\\n\\t"')
         text.extend(case_lines(J))
         text.append('        "SE:\\n\\t}"')
         text.append("        : " + outs)

@@ -286,10 +286,10 @@ struct StripArgs {
     StripGeom g;
     StripTables t;
     int max_items;
-    const float2* y;      // sorted coil values, [ncg][M][CPT] (coil c: group c / CPT, slot c % CPT)
-    int C, ncg;           // coils, coil groups of CPT = 32 / NSL coils
+    const float2* y;      // sorted coil values, [ncg][M][CPW] (coil c: group c / CPW, slot c % CPW)
+    int C, ncg;           // coils, coil groups of CPW = 64 / NSL coils (a coil pair per lane)
     float2* grid;         // [K0][K1][C]
-    float2* partial;      // [slots][ncg][kStripW][32]
+    float2* partial;      // [slots][ncg][kStripW][32] coil pairs (float4)
     int* counters;        // [slots][ncg], zero between calls
 };
 cudaError_t launch_spread_strips(const StripArgs& a, cudaStream_t s);

@@ -2,8 +2,8 @@
 // the transpose of the gather, onto the oversampled grid [K0][K1][C], on strip units.
 //
 // A strip unit is NSL grid rows x kStripW columns.  A warp owns one unit (or one
-// part of a unit) for a coil group of CPT = 32 / NSL coils: lane (s, c) holds row
-// R + s, coil c of the group, all kStripW columns, in registers.
+// part of a unit) for a coil group of CPW = 64 / NSL coils: lane (s, p) holds row
+// R + s, coils 2p and 2p + 1 of the group, all kStripW columns, in registers.
 //
 // Sort time (once per omega, read by every adjoint of the same points).  The
 // scatter counts every point as a hit of each unit its window reaches
@@ -16,7 +16,7 @@
 // them in turn from a shared counter, loading the next item's descriptor and hit
 // records while the current one is processed.  A warp takes its item's hits 32 at
 // a time: each lane copies
-// one hit's kernel weights and CPT coil values into the warp's shared staging area
+// one hit's kernel weights and CPW coil values into the warp's shared staging area
 // with asynchronous copies (cp.async), and then every hit is added to the accumulators
 // of all lanes at once: the lane's row tap comes from its row slot, and the column
 // taps land on compile-time register indices through a warp-uniform jump table on
@@ -258,25 +258,24 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Staging rows are XOR-swizzled by the hit index in 16-byte chunks, so that the asynchronous copies
+// of eight lanes (eight hits) and the reads of one hit by all lanes both fall on distinct banks:
+// coil-pair chunk q of hit h sits at q ^ (h mod NQ), weight chunk q at q ^ ((h / 2) mod 4).
 template <int J, int NSL>
-__global__ void __launch_bounds__(kStripWarps * 32, 7) k_spread_strips(StripArgs a) {
+__global__ void __launch_bounds__(kStripWarps * 32, 4) k_spread_strips(StripArgs a) {
     pdl_wait();
-    constexpr int CPT = 32 / NSL;
-    // staging rows padded by 16 bytes, so that the 16-byte asynchronous copies of eight lanes fall on
-    // distinct banks: coil values 2 CPT + 2 floats (at least 4), weights 16 + 4 floats
-    constexpr int YP = (CPT < 2 ? 2 : CPT) + 2;   // in float2
-    constexpr int WP = 20;                        // in float: row taps [0, 8), column taps [8, 16)
-    __shared__ __align__(16) float2 s_y[kStripWarps][kStripBatch][YP];
-    __shared__ __align__(16) float s_w[kStripWarps][kStripBatch][WP];
-    __shared__ int2 s_m[kStripWarps][kStripBatch];   // {start column, start-row offset}
+    constexpr int CPW = 64 / NSL;     // coils per warp (a coil pair per lane)
+    constexpr int NQ = CPW / 2;       // coil pairs = 16-byte chunks per staged hit
+    __shared__ __align__(16) float4 s_y[kStripWarps][kStripBatch][NQ];
+    __shared__ __align__(16) float s_w[kStripWarps][kStripBatch][16];   // row taps chunks 0-1, column taps 2-3
+    __shared__ int2 s_m[kStripWarps][kStripBatch];                      // {start column, start-row offset}
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cg = blockIdx.y;
     const StripGeom g = a.g;
-    const int s = lane / CPT, c = lane - s * CPT;
-    const int coil = cg * CPT + c;
+    const int s = lane / NQ, pc = lane - s * NQ;      // row slot, coil pair
+    const int coil = cg * CPW + 2 * pc;
     const int C = a.C;
-    const bool cok = coil < C;
-    const float2* yg = a.y + (int64_t)cg * a.pts.m * CPT;   // this coil group's values, [M][CPT]
+    const float4* yg = (const float4*)(a.y + (int64_t)cg * a.pts.m * CPW);   // [M][NQ] pairs of this group
     const int nitems = a.t.nitems[0];
     // Block b owns items b, b + gridDim.x, ... (split parts, first in the list, spread over the
     // blocks); its warps take them in turn from a shared counter, so a warp that drew a heavy item
@@ -305,23 +304,20 @@ __global__ void __launch_bounds__(kStripWarps * 32, 7) k_spread_strips(StripArgs
         const int NR = min(NSL, g.K0 - R);
         const int Bt1 = min(kStripW, g.K1 - org1);
 
-        float acc[2 * kStripW];   // column k: real acc[2k], imaginary acc[2k + 1]
+        float acc[4 * kStripW];   // column k: acc[4k .. 4k+3] = re, im of coil 2 pc, then of coil 2 pc + 1
 #pragma unroll
-        for (int k = 0; k < 2 * kStripW; ++k) acc[k] = 0.f;
+        for (int q = 0; q < 4 * kStripW; ++q) acc[q] = 0.f;
         for (int b = item.y; b < item.z; b += kStripBatch) {
             const int nh = min(kStripBatch, item.z - b);
             if (b != item.y && lane < nh) hit = a.t.hits[b + lane];   // later batches of a split part
             if (lane < nh) {
+                const int sw = (lane >> 1) & 3;
                 const float* pw = a.pts.w + (int64_t)hit.x * 16;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) cp_async16(&s_w[warp][lane][4 * q], pw + 4 * q);
-                const float2* py = yg + (int64_t)hit.x * CPT;
-                if constexpr (CPT >= 2) {
+                for (int q = 0; q < 4; ++q) cp_async16(&s_w[warp][lane][4 * (q ^ sw)], pw + 4 * q);
+                const float4* py = yg + (int64_t)hit.x * NQ;
 #pragma unroll
-                    for (int q = 0; q < CPT / 2; ++q) cp_async16(&s_y[warp][lane][2 * q], py + 2 * q);
-                } else {
-                    cp_async8(&s_y[warp][lane][0], py);
-                }
+                for (int q = 0; q < NQ; ++q) cp_async16(&s_y[warp][lane][q ^ (lane & (NQ - 1))], py + q);
                 s_m[warp][lane] = make_int2((hit.y & 255) - 8, (hit.y >> 8) - 32);
             }
             cp_async_wait_all();
@@ -331,12 +327,14 @@ __global__ void __launch_bounds__(kStripWarps * 32, 7) k_spread_strips(StripArgs
                 const int2 m = s_m[warp][h];
                 const int ta = m.y + s;   // this lane's row tap
                 const float* w = s_w[warp][h];
-                const float wo = (unsigned)ta < (unsigned)J ? w[ta] : 0.f;
-                const float2 yv = s_y[warp][h][c];
-                const float4 wa = *(const float4*)(w + 8);
-                const float4 wb = *(const float4*)(w + 12);
+                const int sw = (h >> 1) & 3;
+                const float wo = (unsigned)ta < (unsigned)J ? w[4 * ((ta >> 2) ^ sw) + (ta & 3)] : 0.f;
+                const float4 yv = s_y[warp][h][pc ^ (h & (NQ - 1))];
+                const float4 wa = *(const float4*)(w + 4 * (2 ^ sw));
+                const float4 wb = *(const float4*)(w + 4 * (3 ^ sw));
                 const float wx[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-                strip_add_J<J>(acc, m.x, wx, wo * yv.x, wo * yv.y);
+                const float yw[4] = {wo * yv.x, wo * yv.y, wo * yv.z, wo * yv.w};
+                strip_add_J<J>(acc, m.x, wx, yw);
             }
             __syncwarp();   // the staging area is refilled by the next batch
         }
@@ -349,9 +347,10 @@ __global__ void __launch_bounds__(kStripWarps * 32, 7) k_spread_strips(StripArgs
         if (!write) {   // split unit: deposit this part, count it; the last part adds all parts in order
             const int4 sp = a.t.splits[item.w];
             const int part = sp.x, nparts = sp.y, slot0 = sp.z;
-            float2* pp = a.partial + ((int64_t)(slot0 + part) * a.ncg + cg) * (kStripW * 32);
+            float4* pp = (float4*)a.partial + ((int64_t)(slot0 + part) * a.ncg + cg) * (kStripW * 32);
 #pragma unroll
-            for (int k = 0; k < kStripW; ++k) pp[k * 32 + lane] = make_float2(acc[2 * k], acc[2 * k + 1]);
+            for (int q = 0; q < kStripW; ++q)
+                pp[q * 32 + lane] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
             __threadfence();
             __syncwarp();
             int old = 0;
@@ -360,25 +359,38 @@ __global__ void __launch_bounds__(kStripWarps * 32, 7) k_spread_strips(StripArgs
             if (old == nparts - 1) {
                 __threadfence();
 #pragma unroll
-                for (int k = 0; k < 2 * kStripW; ++k) acc[k] = 0.f;
+                for (int q = 0; q < 4 * kStripW; ++q) acc[q] = 0.f;
                 for (int q2 = 0; q2 < nparts; ++q2) {
-                    const float2* src = a.partial + ((int64_t)(slot0 + q2) * a.ncg + cg) * (kStripW * 32);
+                    const float4* src = (const float4*)a.partial + ((int64_t)(slot0 + q2) * a.ncg + cg) * (kStripW * 32);
 #pragma unroll
-                    for (int k = 0; k < kStripW; ++k) {
-                        const float2 v = __ldcg(src + k * 32 + lane);
-                        acc[2 * k] += v.x;
-                        acc[2 * k + 1] += v.y;
+                    for (int q = 0; q < kStripW; ++q) {
+                        const float4 v = __ldcg(src + q * 32 + lane);
+                        acc[4 * q] += v.x;
+                        acc[4 * q + 1] += v.y;
+                        acc[4 * q + 2] += v.z;
+                        acc[4 * q + 3] += v.w;
                     }
                 }
                 if (lane == 0) a.counters[(int64_t)slot0 * a.ncg + cg] = 0;
                 write = true;
             }
         }
-        if (write && rok && cok) {
+        if (write && rok && coil < C) {
             float2* dst = a.grid + ((int64_t)(R + s) * g.K1 + org1) * C + coil;
+            if (coil + 1 < C && (C & 1) == 0) {   // both coils, one 16-byte store per column
 #pragma unroll
-            for (int k = 0; k < kStripW; ++k)
-                if (k < Bt1) dst[(int64_t)k * C] = make_float2(acc[2 * k], acc[2 * k + 1]);
+                for (int q = 0; q < kStripW; ++q)
+                    if (q < Bt1)
+                        *(float4*)(dst + (int64_t)q * C) = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+            } else {
+                const bool two = coil + 1 < C;
+#pragma unroll
+                for (int q = 0; q < kStripW; ++q)
+                    if (q < Bt1) {
+                        dst[(int64_t)q * C] = make_float2(acc[4 * q], acc[4 * q + 1]);
+                        if (two) dst[(int64_t)q * C + 1] = make_float2(acc[4 * q + 2], acc[4 * q + 3]);
+                    }
+            }
         }
         it = itn;
         item = itemn;
@@ -417,7 +429,6 @@ static void strips_launch(const StripArgs& a, cudaStream_t s) {
 template <int J>
 static cudaError_t strips_j(const StripArgs& a, cudaStream_t s) {
     switch (a.g.NSL) {
-        case 2: strips_launch<J, 2>(a, s); break;
         case 4: strips_launch<J, 4>(a, s); break;
         case 8: strips_launch<J, 8>(a, s); break;
         case 16: strips_launch<J, 16>(a, s); break;

@@ -87,8 +87,8 @@ struct nufft_plan_s {
     // 2-D strip spread: sort keys (bin, start row), strip units of NSL rows x kStripW columns
     bool strip = false;
     int NSL = 2, nunits = 0, strip_P = 64, strip_slots = 0, ncg_max = 1;
-    float2* d_ys = nullptr;        // [ncg_max][M_cap][32 / NSL] coil values in sorted point order
-    float2* d_partial = nullptr;   // [strip_slots][ncg_max][kStripW][32]
+    float2* d_ys = nullptr;        // [ncg_max][M_cap][64 / NSL] coil values in sorted point order
+    float2* d_partial = nullptr;   // [strip_slots][ncg_max][kStripW][32] coil pairs (float4)
     int* d_counters = nullptr;     // [strip_slots][ncg_max], zero between calls
     int* d_hcount = nullptr;       // [nunits] hits per strip unit
     int* d_hcur = nullptr;         // [nunits] fill cursors
@@ -268,12 +268,13 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
     p.cell_spread = p.D >= 2 && tcells <= 512;
     for (int d = 0; d < p.D; ++d) p.cell_spread = p.cell_spread && p.B[d] + p.J - 1 <= p.K[d];
     p.P = p.cell_spread ? (int)tcells : (p.D == 3 ? 1024 : 512);
-    // 2-D strips: lanes are NSL row slots x 32 / NSL coils, the coils chosen from max_coils; a
-    // window must not reach a unit twice along either axis
+    // 2-D strips: lanes are NSL row slots x 32 / NSL coil pairs, chosen from max_coils; a window
+    // must not reach a unit twice along either axis
     {
-        const int cpt = p.maxC >= 9 ? 16 : (p.maxC >= 5 ? 8 : (p.maxC >= 3 ? 4 : (p.maxC == 2 ? 2 : 1)));
-        p.NSL = 32 / cpt;
-        p.ncg_max = (p.maxC + cpt - 1) / cpt;
+        // coils per warp (a coil pair per lane): 16, 8, 4 or 2; NSL = 64 / coils per warp
+        const int cpw = p.maxC >= 9 ? 16 : (p.maxC >= 5 ? 8 : (p.maxC >= 3 ? 4 : 2));
+        p.NSL = 64 / cpw;
+        p.ncg_max = (p.maxC + cpw - 1) / cpw;
         // a window must not reach a unit twice: K1 >= 16 + J - 1 columns, K0 >= NSL + J - 1 rows
         p.strip = p.D == 2 && p.K[1] >= kStripW + p.J - 1 && p.K[0] >= p.NSL + p.J - 1;
         if (o->spread_variant == NUFFT_SPREAD_TILES || o->spread_variant == NUFFT_SPREAD_GENERAL) p.strip = false;
@@ -288,9 +289,9 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
             return fail(NUFFT_ERR_INVALID_ARG, "unknown spread_variant");
         if (p.strip) {
             p.nunits = (int)(((p.K[0] + p.NSL - 1) / p.NSL) * ((p.K[1] + kStripW - 1) / kStripW));
-            // partial-sum slots for split units: ~nunits / 4, at most 16 MB (the sort lengthens the
-            // parts of split units when they would need more)
-            p.strip_slots = std::max(64, std::min(4096 / p.ncg_max, p.nunits / 4));
+            // partial-sum slots for split units (8 KB each): ~nunits / 4, at most 16 MB (the plan
+            // lengthens the parts of split units when they would need more)
+            p.strip_slots = std::max(64, std::min(2048 / p.ncg_max, p.nunits / 4));
         }
     }
     // KB power-series coefficients a_k = (beta^2/4)^k / (k!)^2
@@ -355,7 +356,7 @@ int64_t sort_keys(const nufft_plan_s& p) { return (int64_t)p.nbins; }
 
 size_t strip_bytes(const nufft_plan_s& p) {
     if (!p.strip) return 0;
-    return (size_t)p.strip_slots * (p.ncg_max * (kStripW * 32 * sizeof(float2) + sizeof(int)) + sizeof(int4)) +
+    return (size_t)p.strip_slots * (p.ncg_max * (kStripW * 32 * sizeof(float4) + sizeof(int)) + sizeof(int4)) +
            (size_t)(3 * p.nunits + 3) * sizeof(int);
 }
 
@@ -368,7 +369,7 @@ size_t point_bytes(const nufft_plan_s& p, int64_t cap) {
     size_t b = (size_t)cap * (2 * sizeof(int) + sizeof(int4) + sizeof(float4) + (p.ws + p.D) * sizeof(float)) +
                max_items(p, cap) * sizeof(int4);
     if (p.strip)
-        b += (size_t)cap * ((size_t)p.ncg_max * (32 / p.NSL) * sizeof(float2) + strip_hits_per_point(p) * sizeof(int2));
+        b += (size_t)cap * ((size_t)p.ncg_max * (64 / p.NSL) * sizeof(float2) + strip_hits_per_point(p) * sizeof(int2));
     return b;
 }
 
@@ -383,7 +384,7 @@ int alloc_points(nufft_plan_s* p, int64_t cap) {
     const size_t c = (size_t)std::max<int64_t>(cap, 1);
     if (p->strip) {
         p->hit_cap = (int64_t)c * strip_hits_per_point(*p);
-        if (cudaMalloc(&p->d_ys, c * (size_t)p->ncg_max * (32 / p->NSL) * sizeof(float2)) != cudaSuccess ||
+        if (cudaMalloc(&p->d_ys, c * (size_t)p->ncg_max * (64 / p->NSL) * sizeof(float2)) != cudaSuccess ||
             cudaMalloc(&p->d_hits, (size_t)p->hit_cap * sizeof(int2)) != cudaSuccess) {
             cudaGetLastError();
             return fail(NUFFT_ERR_OOM, "device allocation of the strip hit lists failed");
@@ -730,7 +731,7 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
         ta.t = strip_tables(*p);
         ta.max_items = p->nunits + p->strip_slots;
         ta.C = C;
-        const int cpt = 32 / p->NSL;
+        const int cpt = 64 / p->NSL;   // coils per warp
         ta.ncg = (C + cpt - 1) / cpt;
         ta.grid = p->d_G;
         ta.partial = p->d_partial;
@@ -957,7 +958,7 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
     cudaMemset(p->d_nitems, 0, 2 * sizeof(int));
     if (p->strip) {
         const size_t nslot = (size_t)p->strip_slots * p->ncg_max;
-        if (cudaMalloc(&p->d_partial, nslot * kStripW * 32 * sizeof(float2)) != cudaSuccess ||
+        if (cudaMalloc(&p->d_partial, nslot * kStripW * 32 * sizeof(float4)) != cudaSuccess ||
             cudaMalloc(&p->d_counters, nslot * sizeof(int)) != cudaSuccess ||
             cudaMalloc(&p->d_hcount, (size_t)p->nunits * sizeof(int)) != cudaSuccess ||
             cudaMalloc(&p->d_hcur, (size_t)p->nunits * sizeof(int)) != cudaSuccess ||
@@ -1068,7 +1069,7 @@ int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_
         g.grad = grad_omega;
         if (grad_x && p->strip) {
             g.v_sorted = p->d_ys;
-            g.v_sorted_cpt = 32 / p->NSL;
+            g.v_sorted_cpt = 64 / p->NSL;
             vsorted = p->d_ys;
         } else if (grad_x && p->cell_spread && (size_t)C * (size_t)p->M <= p->T_elems) {
             g.v_sorted = p->d_T;
