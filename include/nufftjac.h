@@ -169,12 +169,16 @@ const char* nufft_last_error(void);
  *   - A problem whose scratch would exceed the array returns
  *     NUFFT_ERR_UNSUPPORTED with the byte counts in nufft_last_error().
  *   - The first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *     that device current) and keeps it for the life of the process; make
+ *     that first call before any stream capture, and do not use the call on a
+ *     device after cudaDeviceReset (the kept address would be stale).
  *   - Every call uses the same array and leaves its contents behind; calls
  *     whose work overlaps on the GPU (other streams, other host threads)
  *     race on it and must be serialised by the caller.  The call itself
  *     zeroes what must start at zero (the sort counters).
- *   - Tables are copied from host memory with cudaMemcpyAsync on `stream`. */
+ *   - The scaling and twiddle tables are computed on the device into the
+ *     array; nothing is copied from host memory and the host does not wait
+ *     for the stream (the call is asynchronous like the others). */
 #define NUFFT_NOALLOC_SCRATCH_BYTES (32u << 20)
 int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float* omega, int C, const nufft_cfloat* x,
                           const nufft_cfloat* smaps, nufft_cfloat* y, void* stream);

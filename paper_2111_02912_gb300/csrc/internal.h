@@ -63,6 +63,7 @@ struct StripTables {
     int* hcur;        // [nunits]   fill cursors (zeroed by the plan)
     int* hoff;        // [nunits+1] first hit of each unit
     int2* hits;       // [hit_cap]
+    int2* fill_to;    // where the fill writes: hits, or a scratch list reordered into hits
     int64_t hit_cap;
     int4* items;      // [nunits + slots]
     int4* splits;     // [slots]
@@ -110,11 +111,17 @@ cudaError_t launch_item_scan(const SortArgs& a, cudaStream_t s);     // item off
 constexpr int kFusedTablesMaxBins = 8192;
 cudaError_t launch_sort_tables(const SortArgs& a, cudaStream_t s);   // the three above in one block
 cudaError_t launch_bin_scatter(const SortArgs& a, cudaStream_t s);   // records and weights in bin order
+// Deterministic order: ranks within each bin by original index (before the scatter; tmp is [M]
+// scratch).  Step 0 places the original indices, step 1 ranks them.
+cudaError_t launch_det_ranks(const SortArgs& a, int step, int* tmp, cudaStream_t s);
 // 2-D strip tables (kernels_strip.cu), after the scatter (which counts the hits per unit):
 cudaError_t launch_strip_plan(const SortArgs& a, int step, cudaStream_t s);   // step 0: block totals; 1: offsets, items
 int strip_plan_blocks(int nunits);   // blocks of the plan launches
 int strip_plan_vals();               // per-block totals the plan keeps
 cudaError_t launch_strip_fill(const SortArgs& a, cudaStream_t s);    // hit lists
+// Deterministic order: the fill writes into hits_tmp, then each unit's hits are ranked by sorted
+// point index into hits.
+cudaError_t launch_strip_order(const SortArgs& a, const int2* hits_tmp, cudaStream_t s);
 
 // Bins whose points can reach tile `bin` (tiles are the bins).  A window
 // covers J cells to the right of its start, so along each axis these are the

@@ -221,6 +221,37 @@ __global__ void __launch_bounds__(1024) k_sort_tables(SortArgs a) {
     }
 }
 
+// Deterministic order (nufft_opts.deterministic): the histogram's ranks within a bin follow the
+// order in which the atomics arrived.  k_det_place writes every point's original index at that
+// position (into the scratch `tmp`, [M]); k_det_rank then gives each point the rank of its original
+// index among the points of its bin, so the scatter orders each bin by original index.
+__global__ void k_det_place(SortArgs a, int* tmp) {
+    pdl_wait();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.m) return;
+    tmp[a.offsets[a.keyid[i]] + a.local[i]] = (int)i;
+}
+
+__global__ void k_det_rank(SortArgs a, const int* tmp) {
+    pdl_wait();
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.m) return;
+    const int i = tmp[j];
+    const int key = a.keyid[i];
+    const int lo = a.offsets[key], hi = a.offsets[key + 1];
+    int rank = 0;
+    for (int t = lo; t < hi; ++t) rank += tmp[t] < i;
+    a.local[i] = rank;
+}
+
+cudaError_t launch_det_ranks(const SortArgs& a, int step, int* tmp, cudaStream_t s) {
+    if (a.m == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((a.m + 255) / 256);
+    if (step == 0) (void)launch_pdl(k_det_place, blocks, 256, 0, s, a, tmp);
+    else (void)launch_pdl(k_det_rank, blocks, 256, 0, s, a, (const int*)tmp);
+    return cudaGetLastError();
+}
+
 __global__ void k_bin_scatter(SortArgs a) {
     pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

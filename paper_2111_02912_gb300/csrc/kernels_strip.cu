@@ -227,8 +227,29 @@ __global__ void k_strip_fill(SortArgs a) {
     const StripTables& T = a.st;
     strip_point_units(a.sg, ix.x, ix.y, [&](int u, int sd, int dr) {
         const int64_t pos = (int64_t)T.hoff[u] + atomicAdd(T.hcur + u, 1);
-        if (pos < T.hit_cap) T.hits[pos] = make_int2((int)p, strip_meta(sd, dr));
+        if (pos < T.hit_cap) T.fill_to[pos] = make_int2((int)p, strip_meta(sd, dr));
     });
+}
+
+// Deterministic order: one warp per unit ranks each of its hits by sorted point index (the indices
+// of a unit are distinct) and writes it at that rank; the fill's order followed its atomics.
+__global__ void k_strip_order(SortArgs a, const int2* __restrict__ tmp) {
+    pdl_wait();
+    const int u = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (u >= a.nunits) return;   // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const int lo = a.st.hoff[u], hi = a.st.hoff[u + 1];
+    for (int h = lo + lane; h < hi; h += 32) {
+        const int2 e = tmp[h];
+        int rank = 0;
+        for (int t = lo; t < hi; ++t) rank += tmp[t].x < e.x;
+        a.st.hits[lo + rank] = e;
+    }
+}
+
+cudaError_t launch_strip_order(const SortArgs& a, const int2* hits_tmp, cudaStream_t s) {
+    (void)launch_pdl(k_strip_order, (unsigned)((a.nunits + 7) / 8), 256, 0, s, a, hits_tmp);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_strip_plan(const SortArgs& a, int step, cudaStream_t s) {

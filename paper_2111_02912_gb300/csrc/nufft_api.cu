@@ -37,12 +37,13 @@ int fail(int status, const std::string& msg) {
 enum ProfKind {
     PK_ZERO, PK_BIN_COUNT, PK_BIN_SCAN, PK_TILE_SCAN, PK_BIN_SCATTER, PK_BIN_ITEMS, PK_FFT_FWD_FIRST, PK_FFT_FWD_MID,
     PK_FFT_INV_MID, PK_FFT_INV_LAST, PK_GATHER_FWD, PK_GATHER_JVP, PK_GATHER_VJP, PK_ZERO_HEAVY, PK_SPREAD, PK_SUM_CHUNKS, PK_PERMUTE_Y,
-    PK_STRIP_PLAN_A, PK_STRIP_PLAN_B, PK_STRIP_FILL, PK_COUNT
+    PK_STRIP_PLAN_A, PK_STRIP_PLAN_B, PK_STRIP_FILL, PK_DET_PLACE, PK_DET_RANK, PK_STRIP_ORDER, PK_COUNT
 };
 const char* kProfNames[PK_COUNT] = {"zero", "bin_count", "bin_scan", "tile_scan", "bin_scatter", "bin_items", "fft_fwd_first",
                                     "fft_fwd_mid", "fft_inv_mid", "fft_inv_last", "gather_fwd", "gather_jvp",
                                     "gather_vjp", "zero_heavy", "spread", "sum_chunks", "permute_y",
-                                    "strip_plan_a", "strip_plan_b", "strip_fill"};
+                                    "strip_plan_a", "strip_plan_b", "strip_fill", "det_place", "det_rank",
+                                    "strip_order"};
 
 int64_t grid_size(int64_t n, double sigma) {
     int64_t k = (int64_t)std::ceil(sigma * (double)n - 1e-9);
@@ -86,6 +87,8 @@ struct nufft_plan_s {
     bool cell_spread = false;   // spread by the row-owner tile kernel (else the general kernel)
     // 2-D strip spread: sort keys (bin, start row), strip units of NSL rows x kStripW columns
     bool strip = false;
+    bool deterministic = false;    // stable bin order and hit lists ordered by sorted point
+    int2* d_hits_tmp = nullptr;    // [hit_cap] the fill's list before ordering (deterministic only)
     int NSL = 2, nunits = 0, strip_P = 64, strip_slots = 0, ncg_max = 1;
     float2* d_ys = nullptr;        // [ncg_max][M_cap][64 / NSL] coil values in sorted point order
     float2* d_partial = nullptr;   // [strip_slots][ncg_max][kStripW][32] coil pairs (float4)
@@ -211,6 +214,7 @@ void free_plan(nufft_plan_s* p) {
     cudaFree(p->d_G); cudaFree(p->d_T);
     cudaFree(p->d_partial); cudaFree(p->d_counters); cudaFree(p->d_ys); cudaFree(p->d_hcount); cudaFree(p->d_hoff);
     cudaFree(p->d_hits); cudaFree(p->d_splits); cudaFree(p->d_hcur); cudaFree(p->d_work); cudaFree(p->d_plan_sums);
+    cudaFree(p->d_hits_tmp);
     if (p->aux) cudaStreamDestroy(p->aux);
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     if (p->join_ev) cudaEventDestroy(p->join_ev);
@@ -287,6 +291,9 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
                                                "most K - J + 1 cells");
         if (o->spread_variant < 0 || o->spread_variant > NUFFT_SPREAD_GENERAL)
             return fail(NUFFT_ERR_INVALID_ARG, "unknown spread_variant");
+        p.deterministic = o->deterministic != 0;
+        if (p.deterministic && !p.strip)
+            return fail(NUFFT_ERR_UNSUPPORTED, "deterministic results need the 2-D strip spread");
         if (p.strip) {
             p.nunits = (int)(((p.K[0] + p.NSL - 1) / p.NSL) * ((p.K[1] + kStripW - 1) / kStripW));
             // partial-sum slots for split units (8 KB each): ~nunits / 4, at most 16 MB (the plan
@@ -369,23 +376,26 @@ size_t point_bytes(const nufft_plan_s& p, int64_t cap) {
     size_t b = (size_t)cap * (2 * sizeof(int) + sizeof(int4) + sizeof(float4) + (p.ws + p.D) * sizeof(float)) +
                max_items(p, cap) * sizeof(int4);
     if (p.strip)
-        b += (size_t)cap * ((size_t)p.ncg_max * (64 / p.NSL) * sizeof(float2) + strip_hits_per_point(p) * sizeof(int2));
+        b += (size_t)cap * ((size_t)p.ncg_max * (64 / p.NSL) * sizeof(float2) +
+                            (p.deterministic ? 2 : 1) * strip_hits_per_point(p) * sizeof(int2));
     return b;
 }
 
 int alloc_points(nufft_plan_s* p, int64_t cap) {
     cudaFree(p->d_items); cudaFree(p->d_local); cudaFree(p->d_keyid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
-    cudaFree(p->d_pw); cudaFree(p->d_om); cudaFree(p->d_ys); cudaFree(p->d_hits);
+    cudaFree(p->d_pw); cudaFree(p->d_om); cudaFree(p->d_ys); cudaFree(p->d_hits); cudaFree(p->d_hits_tmp);
     p->d_items = nullptr; p->d_local = p->d_keyid = nullptr; p->d_pidx = nullptr; p->d_pfrac = nullptr;
     p->d_pw = nullptr;
     p->d_om = nullptr;
     p->d_ys = nullptr;
     p->d_hits = nullptr;
+    p->d_hits_tmp = nullptr;
     const size_t c = (size_t)std::max<int64_t>(cap, 1);
     if (p->strip) {
         p->hit_cap = (int64_t)c * strip_hits_per_point(*p);
         if (cudaMalloc(&p->d_ys, c * (size_t)p->ncg_max * (64 / p->NSL) * sizeof(float2)) != cudaSuccess ||
-            cudaMalloc(&p->d_hits, (size_t)p->hit_cap * sizeof(int2)) != cudaSuccess) {
+            cudaMalloc(&p->d_hits, (size_t)p->hit_cap * sizeof(int2)) != cudaSuccess ||
+            (p->deterministic && cudaMalloc(&p->d_hits_tmp, (size_t)p->hit_cap * sizeof(int2)) != cudaSuccess)) {
             cudaGetLastError();
             return fail(NUFFT_ERR_OOM, "device allocation of the strip hit lists failed");
         }
@@ -412,6 +422,7 @@ StripTables strip_tables(const nufft_plan_s& p) {
     t.partial_sums = p.d_plan_sums;
     t.hoff = p.d_hoff;
     t.hits = p.d_hits;
+    t.fill_to = p.deterministic ? p.d_hits_tmp : p.d_hits;
     t.hit_cap = p.hit_cap;
     t.items = p.d_items;
     t.splits = p.d_splits;
@@ -551,6 +562,11 @@ int sort_rest(nufft_plan_s* p, cudaStream_t s) {
         if ((st = launch(p, PK_BIN_ITEMS, ss, [&] { return launch_item_scan(a, ss); }))) return st;
     }
     if (!capturing) p->kcount_clear = true;
+    if (p->deterministic) {   // bins ordered by original index (the point records' buffer is scratch here)
+        if ((st = launch(p, PK_DET_PLACE, ss, [&] { return launch_det_ranks(a, 0, (int*)p->d_pfrac, ss); })) ||
+            (st = launch(p, PK_DET_RANK, ss, [&] { return launch_det_ranks(a, 1, (int*)p->d_pfrac, ss); })))
+            return st;
+    }
     if ((st = launch(p, PK_BIN_SCATTER, ss, [&] { return launch_bin_scatter(a, ss); }))) return st;
     if (p->aux) {
         NJ_CUDA(cudaEventRecord(p->join_ev, p->aux));
@@ -563,6 +579,9 @@ int sort_rest(nufft_plan_s* p, cudaStream_t s) {
         if ((st = launch(p, PK_STRIP_PLAN_A, ss, [&] { return launch_strip_plan(a, 0, ss); }))) return st;
         if ((st = launch(p, PK_STRIP_PLAN_B, ss, [&] { return launch_strip_plan(a, 1, ss); }))) return st;
         if ((st = launch(p, PK_STRIP_FILL, ss, [&] { return launch_strip_fill(a, ss); }))) return st;
+        if (p->deterministic &&
+            (st = launch(p, PK_STRIP_ORDER, ss, [&] { return launch_strip_order(a, p->d_hits_tmp, ss); })))
+            return st;
         if (p->aux) {
             NJ_CUDA(cudaEventRecord(p->join2_ev, p->aux));
             p->join2_pending = true;
@@ -1199,6 +1218,28 @@ int noalloc_scratch(void** out) {
     return NUFFT_OK;
 }
 
+// Scaling factors s[n] = 1 / psi_hat((n - N/2) / K) (the Kaiser-Bessel transform in closed form, FP64)
+// and twiddles exp(-2 pi i t / L) of one axis, written into the scratch array on the device, so that
+// the call copies nothing from host memory.
+__global__ void k_noalloc_tables(float* deap, int64_t N, int64_t K, int J, double beta, float2* tw, int L) {
+    pdl_wait();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+        const double f = (double)(i - N / 2) / (double)K;
+        const double x = M_PI * J * f;
+        const double q = beta * beta - x * x;
+        double ft = J;
+        if (q > 0) ft = J * sinh(sqrt(q)) / sqrt(q);
+        else if (q < 0) ft = J * sin(sqrt(-q)) / sqrt(-q);
+        deap[i] = (float)(1.0 / ft);
+    }
+    if (i < L) {
+        double sn, cs;
+        sincospi(-2.0 * (double)i / (double)L, &sn, &cs);
+        tw[i] = make_float2((float)cs, (float)sn);
+    }
+}
+
 struct Carve {
     size_t off = 0;
     template <typename T>
@@ -1258,21 +1299,14 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
     if ((st = noalloc_scratch(&base))) return st;
     unsigned char* b = (unsigned char*)base;
     cudaStream_t s = (cudaStream_t)stream;
-    // tables, computed in FP64 on the host and copied into the scratch array
+    // tables, computed in FP64 on the device into the scratch array (nothing is copied from the host)
     for (int d = 0; d < p.D; ++d) {
-        std::vector<float> dp(p.N[d]);
-        for (int64_t n = 0; n < p.N[d]; ++n)
-            dp[n] = (float)(1.0 / kb_ft((double)(n - p.N[d] / 2) / (double)p.K[d], p.J, p.beta));
         const int L = (int)p.K[d];
-        std::vector<float2> tw(L);
-        for (int t = 0; t < L; ++t) {
-            const double ang = -2.0 * M_PI * (double)t / (double)L;
-            tw[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-        }
         p.d_deap[d] = (float*)(b + o_deap[d]);
         p.d_tw[d] = (float2*)(b + o_tw[d]);
-        NJ_CUDA(cudaMemcpyAsync(p.d_deap[d], dp.data(), dp.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-        NJ_CUDA(cudaMemcpyAsync(p.d_tw[d], tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
+        const int64_t n = std::max<int64_t>(p.N[d], L);
+        NJ_CUDA(launch_pdl(k_noalloc_tables, (unsigned)((n + 255) / 256), 256, 0, s, p.d_deap[d], p.N[d], p.K[d], p.J,
+                           p.beta, p.d_tw[d], L));
         build_fft_axis(L, p.axis[d]);
         p.axis[d].tw = p.d_tw[d];
     }

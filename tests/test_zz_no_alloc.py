@@ -61,6 +61,21 @@ def test_noalloc_forward_matches_plan_forward_on_two_calls_in_a_row():
         assert rel(y_static, y_plan) < TOL_SAME
 
 
+def test_noalloc_forward_in_1d_and_3d_and_smaller_after_larger():
+    """The array keeps the last call's contents: a small problem after a larger one (1-D and 3-D
+    layouts of the scratch) must not see them."""
+    from paper_2111_02912_gb300 import _abi
+    cases = [make_case((12, 10, 14), 2500, 2, True, seed=43),   # 3-D
+             make_case((96, 80), 6000, 4, True, seed=44),       # the largest of the sequence
+             make_case((64,), 700, 3, False, seed=45),          # 1-D, far smaller
+             make_case((8, 10, 6), 300, 1, False, seed=46)]     # 3-D again, smaller still
+    for case in cases:
+        y_static = _noalloc_forward(_abi, case)
+        y_plan = _plan_forward(case)
+        assert np.isfinite(y_static).all()
+        assert rel(y_static, y_plan) < TOL_SAME
+
+
 def test_noalloc_forward_refuses_problems_beyond_its_scratch():
     import torch
 
