@@ -45,6 +45,8 @@ def parse():
                     help="radial320: the hot-path step (default); cgsense3d: gradient of an unrolled "
                          "CG-SENSE loss on the 3-D radial workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="radial320: skip the batched, cgsense3d and cuFFT records added to the line")
     ap.add_argument("--sigma", type=float, default=2.0, help="grid oversampling (radial320 workload)")
     ap.add_argument("--J", type=int, default=6, help="interpolation width (radial320 workload)")
     ap.add_argument("--no-graph", action="store_true",
@@ -189,6 +191,8 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    # the oracle's worker processes (spawn) start first and warm up while the GPU work runs
+    pool = OraclePool(16) if rank == 0 and not args.no_cpu_baseline else None
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = make_inputs()
@@ -361,8 +365,17 @@ def run_ours(args):
                        else "eager per-call",
                        "eager_ms_per_step": eager_ms / args.steps},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w)
+    if pool is not None:
+        line["cpu_baseline"] = cpu_baseline(pool, w)
+        pool.close()
+    if not args.no_extras:
+        # the metric's other forms, measured in the same run: the batched path against the plain path,
+        # the 3-D CG-SENSE gradient step, and cuFFT beside the library's FFT passes
+        line["cufft_compare"] = cufft_compare(info, C)
+        line["cufft_compare"]["library_fft_us"] = {k: round(1e3 * v[1] / v[0], 2)
+                                                   for k, v in prof.items() if k.startswith("fft_")}
+        line["batched"], _ = batched_record(20, 3)
+        line["cgsense3d"], _ = cgsense_record(3, 2)
     print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -394,27 +407,64 @@ def source_hash():
 
 # ------------------------------------------------------------------ oracle
 def oracle_step(w, coils):
-    """The oracle's FP64 same-kernel NUFFT on the same step, restricted to `coils` coils."""
+    """The oracle's FP64 same-kernel NUFFT on the same step, restricted to the coils `coils` (a slice)."""
     from oracle import jacobian as jb
     from oracle.nufft import KBNufft
-    S = w["smaps"][:coils]
-    v = w["v"][:coils]
+    S = w["smaps"][coils]
+    v = w["v"][coils]
     op = KBNufft(w["shape"], w["omega"])           # plan = window geometry (set_points)
     jb.sense_forward(op, w["x"], S)
     jb.vjp_omega_x(op, w["x"], v, S)
 
 
-def cpu_baseline(w, coils=2, reps=3):
-    M, D = w["omega"].shape[1], 2
-    times = []
-    for _ in range(reps):
+_POOL_W = None
+
+
+def _pool_init():
+    """Worker set-up: one host thread per worker (the pool supplies the parallelism) and the
+    workload regenerated from its seeds (nothing large crosses the process boundary)."""
+    global _POOL_W
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    sys.path.insert(0, ROOT)
+    _POOL_W = make_inputs()
+
+
+def _pool_step(bounds):
+    oracle_step(_POOL_W, slice(*bounds))
+    return bounds
+
+
+class OraclePool:
+    """The oracle step with its coils split over worker processes (started with spawn, before or
+    apart from any GPU work), one per host core the process may use."""
+
+    def __init__(self, coils):
+        import multiprocessing as mp
+        self.cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        self.workers = max(1, min(self.cores, coils))
+        self.chunks = [(c, c + 1) for c in range(coils)]
+        self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_pool_init)
+        self.pool.map(_pool_step, self.chunks[: self.workers])   # warm the workers (imports, workload)
+
+    def step(self):
         t0 = time.perf_counter()
-        oracle_step(w, coils)
-        times.append(time.perf_counter() - t0)
-    t = float(np.median(times))
-    return {"value": M * coils * (1 + D) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "radial320 step restricted to %d of 16 coils (all 51200 points), median of %d; "
-                      "NumPy FFT and interpolation run on one host thread" % (coils, reps)}
+        self.pool.map(_pool_step, self.chunks, chunksize=1)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(pool, w, reps=3):
+    M, D, C = w["omega"].shape[1], 2, w["C"]
+    t = float(np.median([pool.step() for _ in range(reps)]))
+    return {"value": M * C * (1 + D) / t, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "ms_per_step": 1e3 * t,
+            "sample": "the whole radial320 step (all 16 coils, all 51200 points), median of %d; the oracle as it "
+                      "stands, one coil per task on %d worker processes (one host thread each) over the %d cores "
+                      "this process may use" % (reps, pool.workers, pool.cores)}
 
 
 def run_reference(args):
@@ -422,25 +472,57 @@ def run_reference(args):
     if rank != 0:
         return
     w = make_inputs()
-    M, D, coils = w["omega"].shape[1], 2, 1
+    M, D, C = w["omega"].shape[1], 2, w["C"]
+    pool = OraclePool(C)
     for _ in range(args.warmup):
-        oracle_step(w, coils)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle_step(w, coils)
-        times.append(time.perf_counter() - t0)
+        pool.step()
+    times = [pool.step() for _ in range(args.steps)]
+    pool.close()
     total = float(sum(times))
-    units = M * coils * (1 + D)
+    units = M * C * (1 + D)
     value = units * args.steps / total
+    sample = ("each step: the whole radial320 step (all 16 coils, all 51200 points), one coil per task on %d worker "
+              "processes over %d host cores" % (pool.workers, pool.cores))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "each step: 1 of 16 coils, all 51200 points"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "radial320 step, 1 of 16 coils, all points"},
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ cuFFT, for comparison only
+def cufft_compare(info, C, steps=20):
+    """torch.fft (cuFFT) on the same oversampled grids, timed beside the library's own FFT passes.
+
+    The library's forward FFT is two line passes over the [K0][K1][ch] grid (channels innermost), the
+    first fed straight from the image (scaling, maps and zero padding fused, the zero rows never
+    transformed).  cuFFT is timed on the already padded grid in the same layout (fft over dims 0 and 1
+    of [K0][K1][ch]) and in its preferred layout ([ch][K0][K1]); neither includes the scaling, the
+    maps or the padding."""
+    import torch
+    K0, K1 = info.k[0], info.k[1]
+    out = {"note": "comparison only; the product path never calls cuFFT", "grid": [K0, K1]}
+    for ch in (C, 2 * C):
+        res = {}
+        for name, shape, dims in (("same_layout", (K0, K1, ch), (0, 1)), ("batched_layout", (ch, K0, K1), (1, 2))):
+            x = torch.randn(shape, dtype=torch.complex64, device="cuda")
+            for _ in range(3):
+                torch.fft.fftn(x, dim=dims)
+            torch.cuda.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for a, b in evs:
+                a.record()
+                torch.fft.fftn(x, dim=dims)
+                b.record()
+            torch.cuda.synchronize()
+            ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
+            nbytes = 2 * K0 * K1 * ch * 8 * 2   # two passes, read + write of the full grid
+            res[name] = {"us": round(1e3 * ms, 2), "gbs_two_pass": round(nbytes / (ms / 1e3) / 1e9, 1)}
+            del x
+        out["channels_%d" % ch] = res
+    return out
 
 
 # ------------------------------------------------------------------ 3-D unrolled CG-SENSE
@@ -456,15 +538,14 @@ def cgsense_units(M, C, D, K):
     return M * C * ((4 * K) + (3 * K + 1)) + M * C * D * (2 * K + 1)
 
 
-def run_cgsense3d(args):
+def cgsense_record(steps, warmup):
+    """The 3-D CG-SENSE loss-gradient step: (JSON fields, value, ms per step, clocks)."""
     import torch
 
     from paper_2111_02912_gb300 import nufft_launch_count
     from paper_2111_02912_gb300.autograd import NufftOperator, cg_sense_unrolled, nufft
     from paper_2111_02912_gb300.workloads import workload
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    dev = torch.device("cuda", torch.cuda.current_device())
     w = workload("radial3d")
     C, M, D = w["C"], w["omega"].shape[1], 3
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -483,13 +564,13 @@ def run_cgsense3d(args):
         loss.backward()
         return loss
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(1, warmup)):
         step()
     torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     n0 = nufft_launch_count()
     torch.cuda.reset_peak_memory_stats()
-    with ClockSampler(local) as clk:
+    with ClockSampler(dev.index or 0) as clk:
         for a, b in evs:
             a.record(stream)
             step()
@@ -498,42 +579,53 @@ def run_cgsense3d(args):
     n1 = nufft_launch_count()
     ms = [a.elapsed_time(b) for a, b in evs]
     units = cgsense_units(M, C, D, CG_ITERS)
-    line = {"metric": METRIC, "value": units / (float(np.mean(ms)) / 1e3), "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": float(np.mean(ms)),
-            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 complex)",
+    rec = {"workload": "cgsense3d: 128x128x96 image, 8 coils, 2,000,000 points (8000 3-D radial spokes x 250, "
+                       "random-walk perturbed); loss = ||x_K - x||^2, x_K = %d unrolled CG-SENSE iterations on "
+                       "(E'E + lam I) x = E'y, lam = 1e-3 M; backward with per-iteration recomputation; gradient "
+                       "w.r.t. omega (D = 3)" % CG_ITERS,
+           "value": units / (float(np.mean(ms)) / 1e3), "unit": UNIT, "ms_per_step": float(np.mean(ms)),
+           "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)), "steps": steps,
+           "units_per_step": units, "peak_device_bytes": int(torch.cuda.max_memory_allocated()),
+           "plan_workspace_bytes": int(op.plan.info().workspace_bytes), "gpu_launches": n1 - n0,
+           "l2": "inputs larger than L2"}
+    return rec, clk.summary()
+
+
+def run_cgsense3d(args):
+    ws, rank, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    rec, clocks = cgsense_record(args.steps, max(3, args.warmup))
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": rec["ms_per_step"], "p50_ms": rec["p50_ms"],
+            "p99_ms": rec["p99_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 (fp32 complex)",
             "data": "synthetic (seeded 3-D radial with random walk, ellipsoid phantom, Gaussian-bump maps)",
-            "config": {"workload": "cgsense3d: 128x128x96 image, 8 coils, 2,000,000 points (8000 3-D radial "
-                                   "spokes x 250, random-walk perturbed); loss = ||x_K - x||^2, x_K = %d unrolled "
-                                   "CG-SENSE iterations on (E'E + lam I) x = E'y, lam = 1e-3 M; backward with "
-                                   "per-iteration recomputation; gradient w.r.t. omega (D = 3)" % CG_ITERS,
-                       "units_per_step": units, "l2": "inputs larger than L2",
-                       "peak_device_bytes": int(torch.cuda.max_memory_allocated()),
-                       "plan_workspace_bytes": int(op.plan.info().workspace_bytes)},
-            "gpu_launches": n1 - n0, "clocks": clk.summary()}
+            "config": {k: rec[k] for k in ("workload", "units_per_step", "l2", "peak_device_bytes",
+                                           "plan_workspace_bytes")},
+            "gpu_launches": rec["gpu_launches"], "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
 
 
 # ------------------------------------------------------------------ batched uneven problems
-def run_batched(args):
+def batched_record(steps, warmup):
+    """64 uneven problems: the captured-graph batch against the plain per-call path."""
     import torch
 
     from paper_2111_02912_gb300 import nufft_launch_count
     from paper_2111_02912_gb300.batch import BatchedJacobian
     from paper_2111_02912_gb300.workloads import batched_problems
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
     probs = batched_problems(64)
     bj = BatchedJacobian(probs, device="cuda", streams=4, autotune=True)
     units = bj.units()
     stream = torch.cuda.current_stream()
 
     def timed(fn):
-        for _ in range(max(3, args.warmup)):
+        for _ in range(max(1, warmup)):
             fn()
         torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         n0 = nufft_launch_count()
         for a, b in evs:
             a.record(stream)
@@ -544,25 +636,37 @@ def run_batched(args):
 
     ms_plain, launches_plain = timed(bj.run_plain)
     bj.capture()
-    with ClockSampler(local) as clk:
+    with ClockSampler(torch.cuda.current_device()) as clk:
         ms_graph, _ = timed(bj.replay)
-    total = sum(ms_graph)
-    line = {"metric": METRIC, "value": units * args.steps / (total / 1e3), "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total / args.steps,
-            "p50_ms": float(np.percentile(ms_graph, 50)), "p99_ms": float(np.percentile(ms_graph, 99)),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 complex)",
-            "data": "synthetic (seeded uneven radial problems)",
-            "config": {"workload": "batched: 64 independent 2-D problems, side uniform over {64,...,384}, M uniform "
-                                   "4000-200000 random-angle radial points (spokes of 2N), coils uniform 1-32; per "
-                                   "problem set_points + forward + vjp(grad_omega, grad_x); autotuned bin shapes; one "
-                                   "CUDA graph over 4 streams",
-                       "units_per_step": units, "points": sum(it.M for it in bj.items),
-                       "plain_value": units * args.steps / (sum(ms_plain) / 1e3),
-                       "plain_ms_per_step": sum(ms_plain) / args.steps,
-                       "speedup_vs_plain": sum(ms_plain) / total,
-                       "bin_sizes": {str(k): v for k, v in bj.tuner.cache.items()},
-                       "l2": "inputs larger than L2"},
-            "gpu_launches": launches_plain, "clocks": clk.summary()}
+    picks = {}
+    for it in bj.items:
+        k = "%s,%s,%s" % it.config if it.config else "default"
+        picks[k] = picks.get(k, 0) + 1
+    rec = {"workload": "batched: 64 independent 2-D problems, side uniform over {64,...,384}, M uniform 4000-200000 "
+                       "random-angle radial points (spokes of 2N), coils uniform 1-32; per problem set_points + "
+                       "forward + vjp(grad_omega, grad_x); autotuned configuration; one CUDA graph over 4 streams",
+           "value": units * steps / (sum(ms_graph) / 1e3), "unit": UNIT, "ms_per_step": sum(ms_graph) / steps,
+           "p50_ms": float(np.percentile(ms_graph, 50)), "p99_ms": float(np.percentile(ms_graph, 99)),
+           "plain_value": units * steps / (sum(ms_plain) / 1e3), "plain_ms_per_step": sum(ms_plain) / steps,
+           "plain_p50_ms": float(np.percentile(ms_plain, 50)), "plain_p99_ms": float(np.percentile(ms_plain, 99)),
+           "speedup_vs_plain": sum(ms_plain) / sum(ms_graph), "steps": steps, "units_per_step": units,
+           "points": sum(it.M for it in bj.items), "configs_picked": picks,
+           "config_candidates": "(spread kernel, bin shape, hits per strip part)", "gpu_launches_plain": launches_plain,
+           "l2": "inputs larger than L2"}
+    return rec, clk.summary()
+
+
+def run_batched(args):
+    ws, rank, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    rec, clocks = batched_record(args.steps, max(3, args.warmup))
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": rec["ms_per_step"], "p50_ms": rec["p50_ms"],
+            "p99_ms": rec["p99_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 (fp32 complex)", "data": "synthetic (seeded uneven radial problems)",
+            "config": {k: v for k, v in rec.items() if k not in ("value", "unit", "ms_per_step", "p50_ms", "p99_ms")},
+            "gpu_launches": rec["gpu_launches_plain"], "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
 

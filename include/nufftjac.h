@@ -79,7 +79,9 @@ typedef struct {
                           adjoint adds its terms in an order fixed by the sort); 0: fastest
                           order (the adjoint then agrees to rounding between calls) */
     int spread_variant; /* adjoint spread kernel: NUFFT_SPREAD_AUTO (0), _STRIPS, _TILES, _GENERAL */
-    int reserved[2];
+    int strip_part;   /* strip spread: hits one warp adds before a unit is split into parts
+                         (a power of two, 8..4096; 0 -> 64) */
+    int reserved[1];
 } nufft_opts;
 
 /* Adjoint spread kernels (nufft_opts.spread_variant), all computing the transpose of the

@@ -33,7 +33,7 @@ class nufft_opts(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("sigma", ctypes.c_double),
                 ("J", ctypes.c_int), ("beta", ctypes.c_double), ("max_coils", ctypes.c_int),
                 ("bin_size", ctypes.c_int * 3), ("deterministic", ctypes.c_int), ("spread_variant", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("strip_part", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class nufft_plan_info(ctypes.Structure):

@@ -10,8 +10,12 @@ a batch:
   dealt round-robin to several streams so that independent problems overlap;
   a step is then one graph launch.
 
-The autotuner picks each problem's spread tile shape (bin_size) by timing one
-step per candidate on the device, cached per (shape, coils, log2 M) class.
+The autotuner times one step per candidate configuration on the device and keeps
+the fastest, cached per (shape, coils, log2 M) class.  A configuration is the
+adjoint spread kernel (register strips or shared-memory tiles), the bin shape of
+the sort (the locality of the gathers' tap reads, and the tile of the tile spread)
+and, for the strips, the hits one warp adds before a unit is split into parts (the
+work per warp).
 """
 import math
 
@@ -19,14 +23,25 @@ import torch
 
 from .plan import Plan
 
-BIN_CANDIDATES_2D = ((16, 16), (16, 32), (32, 16), (8, 32))
+# (spread kernel, bin shape, strip part); the tile kernel ignores the strip part
+CONFIG_CANDIDATES_2D = (
+    ("strips", (16, 16), 64), ("strips", (16, 16), 32), ("strips", (16, 16), 128), ("strips", (32, 32), 64),
+    ("tiles", (16, 16), 0), ("tiles", (16, 32), 0),
+)
+BIN_CANDIDATES_2D = tuple(sorted({c[1] for c in CONFIG_CANDIDATES_2D}))
+
+
+def plan_for(item, config):
+    spread, bins, part = config
+    return Plan(item.shape, item.om, max_coils=item.C, bin_size=bins, spread=spread, strip_part=part)
 
 
 class Autotuner:
-    def __init__(self, candidates=BIN_CANDIDATES_2D, reps=3):
+    def __init__(self, candidates=CONFIG_CANDIDATES_2D, reps=3):
         self.candidates = tuple(candidates)
         self.reps = reps
         self.cache = {}
+        self.timings = {}
 
     @staticmethod
     def key(shape, C, M):
@@ -36,11 +51,14 @@ class Autotuner:
         k = self.key(item.shape, item.C, item.M)
         if k in self.cache:
             return self.cache[k]
-        best, best_ms = None, float("inf")
-        for b in self.candidates:
-            if any(bd > n * 2 for bd, n in zip(b, item.shape)):
+        best, best_ms, times = None, float("inf"), {}
+        for cfg in self.candidates:
+            if any(bd > n * 2 for bd, n in zip(cfg[1], item.shape)):
                 continue
-            plan = Plan(item.shape, item.om, max_coils=item.C, bin_size=b)
+            try:
+                plan = plan_for(item, cfg)
+            except RuntimeError:   # the kernel does not apply to this problem (NUFFT_ERR_UNSUPPORTED)
+                continue
             run = lambda: _step(plan, item)
             run()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -50,10 +68,12 @@ class Autotuner:
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / self.reps
+            times[cfg] = ms
             if ms < best_ms:
-                best, best_ms = b, ms
+                best, best_ms = cfg, ms
             del plan
         self.cache[k] = best
+        self.timings[k] = times
         return best
 
 
@@ -70,7 +90,7 @@ class _Item:
         self.gx = torch.empty(self.shape if self.S is not None else (self.C,) + self.shape,
                               dtype=torch.complex64, device=device)
         self.plan = None
-        self.bin_size = None
+        self.config = None
 
 
 def _step(plan, it):
@@ -87,8 +107,8 @@ class BatchedJacobian:
         self.items = [_Item(p, self.device) for p in problems]
         self.tuner = tuner if tuner is not None else (Autotuner() if autotune else None)
         for it in self.items:
-            it.bin_size = self.tuner.choose(it) if self.tuner is not None else None
-            it.plan = Plan(it.shape, it.om, max_coils=it.C, bin_size=it.bin_size)
+            it.config = self.tuner.choose(it) if self.tuner is not None else None
+            it.plan = plan_for(it, it.config) if it.config is not None else Plan(it.shape, it.om, max_coils=it.C)
         self.nstreams = max(1, int(streams))
         self.graph = None
 

@@ -291,6 +291,11 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
                                                "most K - J + 1 cells");
         if (o->spread_variant < 0 || o->spread_variant > NUFFT_SPREAD_GENERAL)
             return fail(NUFFT_ERR_INVALID_ARG, "unknown spread_variant");
+        if (o->strip_part) {
+            if (o->strip_part < 8 || o->strip_part > 4096 || (o->strip_part & (o->strip_part - 1)))
+                return fail(NUFFT_ERR_INVALID_ARG, "strip_part must be a power of two in [8, 4096]");
+            p.strip_P = o->strip_part;
+        }
         p.deterministic = o->deterministic != 0;
         if (p.deterministic && !p.strip)
             return fail(NUFFT_ERR_UNSUPPORTED, "deterministic results need the 2-D strip spread");

@@ -29,7 +29,7 @@ def _stream():
 
 class Plan:
     def __init__(self, shape, omega, J=6, sigma=2.0, beta=None, max_coils=1, bin_size=None, spread="auto",
-                 deterministic=False):
+                 deterministic=False, strip_part=0):
         self.shape = tuple(int(n) for n in shape)
         self.D = len(self.shape)
         opts = _abi.nufft_default_opts(self.D, self.shape)
@@ -42,6 +42,7 @@ class Plan:
                 opts.bin_size[d] = int(b)
         opts.spread_variant = _abi.SPREAD_VARIANTS[spread]
         opts.deterministic = 1 if deterministic else 0
+        opts.strip_part = int(strip_part)
         self.max_coils = int(max_coils)
         self._omega = omega
         self.M = int(omega.shape[1])
