@@ -279,9 +279,9 @@ def test_launch_counter_and_profile_hooks():
 
 
 def test_radial3d_full_size_sampled_against_exact_nudft():
-    """128x128x96, 8 coils, 2,000,000 perturbed 3-D radial points: y and grad_omega on a point sample.
-
-    Both outputs at point i depend on that point only, so the exact NUDFT of a sample is an exact check."""
+    """128x128x96, 8 coils, 2,000,000 perturbed 3-D radial points: y and grad_omega on a point sample
+    (each depends on its own point only, so the exact NUDFT of a sample is an exact check), and
+    grad_x (the 3-D adjoint spread, heavy tiles included) on a voxel sample against the exact sum."""
     import torch
 
     from paper_2111_02912_gb300 import Plan
@@ -293,14 +293,29 @@ def test_radial3d_full_size_sampled_against_exact_nudft():
     plan = Plan(w["shape"], to_dev(w["omega"]), max_coils=C)
     X, S, V = to_dev(w["x"]), to_dev(w["smaps"]), to_dev(v)
     y = host(plan.forward(X, S))
-    go, _ = plan.vjp_omega_x(X, V, S, need_x=False)
-    go = host(go)
+    go, gx = plan.vjp_omega_x(X, V, S)
+    go, gx = host(go), host(gx)
     torch.cuda.synchronize()
     sub = np.sort(g.choice(M, 300, replace=False))
     ex = NUDFT(w["shape"], w["omega"][:, sub])
     assert rel(y[:, sub], jb.sense_forward(ex, w["x"], w["smaps"])) < TOL_EXACT
     ge, _ = jb.vjp_omega_x(ex, w["x"], v[:, sub], w["smaps"])
     assert rel(go[:, sub], ge) < TOL_GRAD_EXACT
+    # grad_x = E'v, Sec. II-D with the maps of Sec. II-G, depends on all 2 M points: the exact sum
+    # sum_c conj(s_c,j) sum_i v_ci exp(+i omega_i . r_j) on 200 sampled voxels, in FP64, point chunks
+    from oracle.nudft import voxel_centres
+    r = np.stack([c.ravel() for c in np.meshgrid(*voxel_centres(w["shape"]), indexing="ij")])   # (3, N)
+    vox = np.sort(g.choice(r.shape[1], 200, replace=False))
+    rs = r[:, vox].astype(np.float64)
+    om64 = w["omega"].astype(np.float64)
+    acc = np.zeros((C, vox.size), np.complex128)
+    for i0 in range(0, M, 100_000):
+        ph = np.exp(1j * (om64[:, i0:i0 + 100_000].T @ rs))                 # (chunk, 200)
+        acc += v[:, i0:i0 + 100_000].astype(np.complex128) @ ph
+    gx_exact = np.sum(np.conj(w["smaps"].reshape(C, -1)[:, vox].astype(np.complex128)) * acc, axis=0)
+    gx_s = gx.reshape(-1)[vox]
+    assert rel(gx_s, gx_exact) < TOL_EXACT
+    assert max_rel(gx_s, gx_exact) < TOL_EXACT
 
 
 @pytest.mark.parametrize("name,shape,M,C,clustered", [
