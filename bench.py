@@ -2,7 +2,7 @@
 
 One step = nufft_set_points (bin sort of omega) + nufft_forward (y = E x) +
 nufft_vjp_omega_x (grad_omega by the fused interpolation epilogue, grad_x =
-E' v by the tiled spread): every row of the hot path on one batch.
+E' v by the register-strip spread): every row of the hot path on one batch.
 Throughput unit: non-uniform points x channels per second, with channels =
 C (1 + D) per step (C coils, the plain image plus D coordinate-weighted
 images per coil).
@@ -49,6 +49,12 @@ def parse():
                     help="radial320: skip the batched, cgsense3d and cuFFT records added to the line")
     ap.add_argument("--sigma", type=float, default=2.0, help="grid oversampling (radial320 workload)")
     ap.add_argument("--J", type=int, default=6, help="interpolation width (radial320 workload)")
+    ap.add_argument("--spread", default="auto", choices=["auto", "strips", "tiles", "general"],
+                    help="radial320: adjoint spread kernel (auto: the library's choice, register strips in 2-D)")
+    ap.add_argument("--serve-problems", type=int, default=64,
+                    help="serving: distinct problems (trajectory + maps) the requests draw from")
+    ap.add_argument("--serve-fuse", type=int, default=8,
+                    help="serving: most same-problem reconstructions fused into one job (1: no fusion)")
     ap.add_argument("--no-graph", action="store_true",
                     help="radial320: time the eager per-call step only (default: replay the step from a CUDA graph)")
     return ap.parse_args()
@@ -200,7 +206,7 @@ def run_ours(args):
     units = M * C * (1 + D)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     om, X, S, V = t(w["omega"]), t(w["x"]), t(w["smaps"]), t(w["v"])
-    plan = Plan(w["shape"], om, max_coils=C, J=args.J, sigma=args.sigma)
+    plan = Plan(w["shape"], om, max_coils=C, J=args.J, sigma=args.sigma, spread=args.spread)
     y = torch.empty((C, M), dtype=torch.complex64, device=dev)
     go = torch.empty((D, M), dtype=torch.float32, device=dev)
     gx = torch.empty(tuple(w["shape"]), dtype=torch.complex64, device=dev)
@@ -284,7 +290,7 @@ def run_ours(args):
     roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)"
             if hbm_src == "measured" else "fallback",
-            "traffic": traffic_for(name), "algorithmic_bytes_per_launch": int(algo.get(name, 0)),
+            "traffic": traffic_for(name) if args.spread == "auto" else None, "algorithmic_bytes_per_launch": int(algo.get(name, 0)),
             "launch_ms": round(per_launch_ms, 5), "share_of_step": round(kms / sum(v[1] for v in prof.values()), 3),
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 4), "gbs": round(algo[k] * v[0] / (v[1] / 1e3) / 1e9, 1)
                             if k in algo else None} for k, v in prof.items()},
@@ -354,7 +360,7 @@ def run_ours(args):
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
-            "accuracy": {"sigma": args.sigma, "J": args.J},
+            "accuracy": {"sigma": args.sigma, "J": args.J}, "spread": args.spread,
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 complex)",
             "data": "synthetic (seeded; shapes of the paper's 2-D multicoil radial case)",
@@ -399,7 +405,7 @@ def source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2111_02912_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name.endswith((".cu", ".cuh", ".h", ".inc")):
             h.update(name.encode())
             h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
@@ -616,7 +622,7 @@ def batched_record(steps, warmup):
     from paper_2111_02912_gb300 import nufft_launch_count
     from paper_2111_02912_gb300.batch import BatchedJacobian
     from paper_2111_02912_gb300.workloads import batched_problems
-    probs = batched_problems(64)
+    probs = batched_problems(args.serve_problems)
     bj = BatchedJacobian(probs, device="cuda", streams=4, autotune=True)
     units = bj.units()
     stream = torch.cuda.current_stream()
@@ -680,7 +686,7 @@ def run_serving(args, rate=200.0, seconds=3.0):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    probs = batched_problems(64)
+    probs = batched_problems(args.serve_problems)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     pool = [dict(shape=p["shape"], om=t(p["omega"]), S=t(p["smaps"]), x=t(p["x"]), y=t(p["v"]), C=p["C"],
                  M=p["omega"].shape[1]) for p in probs]
@@ -694,10 +700,15 @@ def run_serving(args, rate=200.0, seconds=3.0):
         q = pool[j]
         return Request(i, kind, q["shape"], q["om"], q["S"], x=q["x"], y=q["y"], lam=1e-3, iters=15)
 
-    srv = Server(budget_bytes=120 << 30, slots=8, device=dev)
+    srv = Server(budget_bytes=120 << 30, slots=8, device=dev, fuse=args.serve_fuse)
     for j in range(len(pool)):                  # warm-up: resident plans for every problem class
         srv.submit(make(-1, j, "recon"))
     srv.drain()
+    if args.serve_fuse > 1:
+        for j in range(len(pool)):              # and for fused jobs (one plan serves every job size)
+            srv.submit(make(-1, j, "recon"))
+            srv.submit(make(-1, j, "recon"))
+        srv.drain()
     srv.done.clear()
 
     def units(r, q):
@@ -720,13 +731,16 @@ def run_serving(args, rate=200.0, seconds=3.0):
     lat = latency_summary(done)
     line = {"metric": METRIC, "value": tot_units / wall, "unit": UNIT, "n_gpus": ws, "steps": len(done),
             "warmup": len(pool), "ms_per_step": 1e3 * wall / len(done), "p50_ms": lat["p50_ms"],
-            "p99_ms": lat["p99_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "p99_ms": lat["p99_ms"], "latency_phases": {k: lat[k] for k in (
+                "wait_p50_ms", "wait_p99_ms", "exec_p50_ms", "exec_p99_ms", "fused_requests", "mean_job_size")},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64 (fp32 complex)", "data": "synthetic (seeded uneven radial problems, Poisson arrivals)",
             "config": {"workload": "serving: Poisson arrivals at %.0f req/s for %.1f s; each request picks one of "
-                                   "64 uneven 2-D problems (sides 64-384, M 4k-200k, coils 1-32) and is a CG-SENSE "
+                                   "%d uneven 2-D problems (sides 64-384, M 4k-200k, coils 1-32) and is a CG-SENSE "
                                    "reconstruction (15 iterations of E'E + 1e-3 I) or a trajectory gradient of "
                                    "||E x - y||^2 (50/50); 8 slots (streams), 120 GiB admission budget, resident "
-                                   "plans" % (rate, seconds),
+                                   "plans, same-problem reconstructions fused up to %d per job"
+                                   % (rate, seconds, len(pool), args.serve_fuse),
                        "requests": len(done), "requests_per_s": len(done) / wall, "wall_s": wall,
                        "latency_mean_ms": lat["mean_ms"], "l2": "inputs larger than L2"},
             "clocks": clk.summary()}

@@ -64,6 +64,9 @@ enum {
                                    another kernel, a flag or another GPU */
 };
 
+/* Largest channel count of one call (coils, or images of a map-free call). */
+#define NUFFT_MAX_COILS 128
+
 /* Plan options.  Fields left 0 take the defaults noted. */
 typedef struct {
     int dim;          /* D, 1..3 */
@@ -73,7 +76,7 @@ typedef struct {
     int J;            /* interpolation width, 4..8 (0 -> 6) */
     double beta;      /* Kaiser-Bessel shape (<= 0 -> Beatty et al.:
                          pi sqrt((J/sigma)^2 (sigma-1/2)^2 - 0.8)) */
-    int max_coils;    /* largest C any call on this plan will pass, 1..128 (0 -> 1) */
+    int max_coils;    /* largest C any call on this plan will pass, 1..NUFFT_MAX_COILS (0 -> 1) */
     int bin_size[3];  /* spread tile edge per dim (0 -> automatic: 256, 16x16, 8x8x8) */
     int deterministic; /* 1: every output is bitwise reproducible from call to call (the 2-D
                           adjoint adds its terms in an order fixed by the sort); 0: fastest

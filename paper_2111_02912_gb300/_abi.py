@@ -27,6 +27,7 @@ EXPORTED = (
 )
 
 NUFFT_NOALLOC_SCRATCH_BYTES = 32 << 20
+NUFFT_MAX_COILS = 128
 
 
 class nufft_opts(ctypes.Structure):

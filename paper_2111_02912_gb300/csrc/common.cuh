@@ -61,6 +61,7 @@ struct FftAxis {
     int nstages;
     FftStage st[kMaxStages];
     const float2* tw;   // exp(-2 pi i t / L), t < L (device)
+    const float2* tw2;  // two-phase kernels, L = L1 L2: exp(-2 pi i n2 k1 / L) at n2 L1 + k1 (device)
 };
 
 __device__ __forceinline__ uint32_t div_magic(uint32_t n, uint32_t d, uint32_t magic) {

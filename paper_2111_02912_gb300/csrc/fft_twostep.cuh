@@ -67,10 +67,11 @@ __global__ void __maxnreg__((KIND == PASS_INV_LAST || L2 != 32) ? 128 : 80) k_li
     const int tid = threadIdx.x;
     const int line = tid & (TL - 1), col = tid >> lgTL;
     const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
-    const int64_t bid = blockIdx.x;
-    const int64_t tile_s = bid % a.ntiles_s;
-    const int64_t b0 = (bid / a.ntiles_s) * TB, s0 = tile_s * TS;
+    uint32_t tile_b, tile_s;
+    line_tile(a.ntiles_s, tile_b, tile_s);
+    const int64_t b0 = (int64_t)tile_b * TB, s0 = (int64_t)tile_s * TS;
     const int64_t S = a.S;
+    const int Si = (int)a.S;   // fits in 32 bits (checked when the plan is made)
     const int64_t b = b0 + (line >> lgTS), sl = s0 + (line & (TS - 1));
     const bool valid = b < a.B && sl < S;
     float2* row = buf + line * LP;
@@ -92,7 +93,7 @@ __global__ void __maxnreg__((KIND == PASS_INV_LAST || L2 != 32) ? 128 : 80) k_li
             float rs = 0.f, wr = 0.f;
             int kind = -1;
             if (ok) {
-                const int dblk = (int)(ss / a.im.C), c = (int)(ss - (int64_t)dblk * a.im.C);
+                const int dblk = (int)ss / a.im.C, c = (int)ss - dblk * a.im.C;
                 kind = a.im.has_plain ? dblk - 1 : dblk;
                 float r0, r1;
                 image_row_factors(a.im, bb, rs, r0, r1);
@@ -166,23 +167,23 @@ __global__ void __maxnreg__((KIND == PASS_INV_LAST || L2 != 32) ? 128 : 80) k_li
                     const int p = n1 * L2 + n2;
                     const bool keep = valid && (p < h || p >= L - h);
                     const int e = p < h ? p + h : p - (L - h);
-                    v[n1] = keep ? __ldg(in_line + e * S) : make_float2(0.f, 0.f);
+                    v[n1] = keep ? __ldg(in_line + (int64_t)e * Si) : make_float2(0.f, 0.f);
                 });
             } else {
                 sfor<0, L1>([&](auto n1_) {
                     constexpr int n1 = decltype(n1_)::value;
                     const int p = n1 * L2 + n2;
-                    const float2 t = __ldg(in_line + (valid ? p : 0) * S);   // unconditional load
+                    const float2 t = __ldg(in_line + (int64_t)(valid ? p : 0) * Si);   // unconditional load
                     v[n1] = valid ? t : make_float2(0.f, 0.f);
                 });
             }
         }
         dft<L1, DIR>(v);
         if (n2 > 0) {
-            const float2* tw = a.ax.tw;   // exp(-2 pi i t / L); n2 k1 < L
+            const float2* tw = a.ax.tw2 + n2 * L1;   // row n2: exp(-2 pi i n2 k1 / L) at k1
             sfor<1, L1>([&](auto k1_) {
                 constexpr int k1 = decltype(k1_)::value;
-                float2 w = __ldg(tw + n2 * k1);
+                float2 w = __ldg(tw + k1);
                 if (DIR > 0) w.y = -w.y;
                 v[k1] = cmul(v[k1], w);
             });
@@ -207,10 +208,10 @@ __global__ void __maxnreg__((KIND == PASS_INV_LAST || L2 != 32) ? 128 : 80) k_li
 
     if (KIND == PASS_FWD_FIRST || KIND == PASS_FWD_MID) {
         if (k1 < L1 && valid) {
-            float2* out_line = a.out + b * (int64_t)L * S + sl;
+            float2* out_line = a.out + b * (int64_t)L * S + sl + (int64_t)k1 * Si;
             sfor<0, L2>([&](auto k2_) {
                 constexpr int k2 = decltype(k2_)::value;
-                out_line[(k1 + L1 * k2) * S] = w[k2];
+                out_line[(int64_t)(L1 * k2) * Si] = w[k2];
             });
         }
     } else if (KIND == PASS_INV_MID) {
@@ -221,7 +222,7 @@ __global__ void __maxnreg__((KIND == PASS_INV_LAST || L2 != 32) ? 128 : 80) k_li
                 constexpr int k2 = decltype(k2_)::value;
                 const int k = k1 + L1 * k2;
                 const int e = k < h ? k + h : k - (L - h);
-                if (k < h || k >= L - h) out_line[e * S] = w[k2];
+                if (k < h || k >= L - h) out_line[(int64_t)e * Si] = w[k2];
             });
         }
     } else {   // PASS_INV_LAST: crop into shared memory, then the image side

@@ -204,7 +204,7 @@ struct LinePass {
     int64_t B, S;          // outer lines, inner stride (complex elements)
     int TB, TS, lgTS, lgTL, TLP;
     int nchunks;           // coil-sum epilogue: channel chunks looped in one block
-    int64_t ntiles_s;      // channel tiles per row tile (the grid is flat: ntiles_b * ntiles_s blocks)
+    int64_t ntiles_s;      // channel tiles per row tile (see line_grid)
     int coil_sum;
     const float2* in;
     float2* out;
@@ -213,6 +213,25 @@ struct LinePass {
     uint32_t magic_n;      // ceil(2^32 / n) for the axis length used in index maps
 };
 enum PassKind { PASS_FWD_FIRST, PASS_FWD_MID, PASS_INV_MID, PASS_INV_LAST };
+// Launch grid of a line pass: (row tile, channel tile) as blockIdx (x, y) when the channel tiles fit
+// gridDim.y, else one flat index with channel tiles fastest (then the row tiles fit gridDim.y: the
+// product is at most 2^31 - 1).  line_tile inverts it without 64-bit division.
+constexpr int64_t kGridYMax = 65535;
+inline dim3 line_grid(int64_t ntiles_b, int64_t ntiles_s) {
+    return ntiles_s <= kGridYMax ? dim3((unsigned)ntiles_b, (unsigned)ntiles_s) : dim3((unsigned)(ntiles_b * ntiles_s));
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ void line_tile(int64_t ntiles_s, uint32_t& tile_b, uint32_t& tile_s) {
+    if (ntiles_s <= kGridYMax) {
+        tile_b = blockIdx.x;
+        tile_s = blockIdx.y;
+    } else {
+        const uint32_t n = (uint32_t)ntiles_s;
+        tile_b = blockIdx.x / n;
+        tile_s = blockIdx.x - tile_b * n;
+    }
+}
+#endif
 cudaError_t launch_line_pass(PassKind kind, const LinePass& a, dim3 grid, int threads, size_t smem,
                              cudaStream_t s);
 // Register-resident two-phase passes (k_line_fft2): factorisations L = L1 L2

@@ -180,10 +180,10 @@ __global__ void __launch_bounds__(256) k_line_fft(LinePass a) {
     float* row_r = row_scale + TB;                        // [TB][2]
     __shared__ FftStage sst[kMaxStages];
     const int tid = threadIdx.x, nt = blockDim.x;
-    // flat grid: block = (row tile, channel tile), channel tiles fastest
-    const int64_t bid = blockIdx.x;
-    const int64_t by = bid % a.ntiles_s;
-    const int64_t b0 = (bid / a.ntiles_s) * TB;
+    uint32_t tile_b, tile_s;
+    line_tile(a.ntiles_s, tile_b, tile_s);
+    const int64_t by = tile_s;
+    const int64_t b0 = (int64_t)tile_b * TB;
 
     for (int i = tid; i < L; i += nt) tw[i] = a.ax.tw[i];
     if (tid == 0) {

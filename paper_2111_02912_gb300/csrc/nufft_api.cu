@@ -233,7 +233,7 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
     p.J = o->J ? o->J : 6;
     if (p.J < kJMin || p.J > kJMax) return fail(NUFFT_ERR_UNSUPPORTED, "J must lie in [4, 8]");
     p.maxC = o->max_coils ? o->max_coils : 1;
-    if (p.maxC < 1 || p.maxC > 128) return fail(NUFFT_ERR_UNSUPPORTED, "max_coils must lie in [1, 128]");
+    if (p.maxC < 1 || p.maxC > NUFFT_MAX_COILS) return fail(NUFFT_ERR_UNSUPPORTED, "max_coils must lie in [1, 128]");
     p.Nimg = 1;
     p.Ktot = 1;
     for (int d = 0; d < p.D; ++d) {
@@ -246,6 +246,10 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
         p.Nimg *= n;
         p.Ktot *= p.K[d];
     }
+    // the line passes index within a line in 32 bits: the channel stride of the first axis,
+    // (1 + D) max_coils prod_{d > 0} K_d complex elements, must fit
+    if ((int64_t)(1 + p.D) * p.maxC * (p.Ktot / p.K[0]) > (int64_t)INT32_MAX)
+        return fail(NUFFT_ERR_UNSUPPORTED, "oversampled grid too large for max_coils");
     p.beta = o->beta > 0 ? o->beta
                          : M_PI * std::sqrt(std::pow(p.J / p.sigma, 2) * std::pow(p.sigma - 0.5, 2) - 0.8);
     // bins = spread tiles of B_d cells per axis; coils per spread block from the tile size
@@ -727,7 +731,7 @@ int forward_grids(nufft_plan_s* p, int C, int nd, int has_plain, const float2* x
         a.magic_L = magic_of((uint32_t)L);
         a.magic_n = magic_of((uint32_t)a.n_out);
         a.ntiles_s = (S + t.TS - 1) / t.TS;
-        dim3 grid((unsigned)(((B + t.TB - 1) / t.TB) * a.ntiles_s));
+        const dim3 grid = line_grid((B + t.TB - 1) / t.TB, a.ntiles_s);
         const PassKind kind = (k == 0) ? PASS_FWD_FIRST : PASS_FWD_MID;
         int st = launch(p, k == 0 ? PK_FFT_FWD_FIRST : PK_FFT_FWD_MID, s, [&] {
             return t.L1 ? launch_line_pass2(kind, t.L1, t.L2, a, grid, t.threads, t.smem, s)
@@ -852,7 +856,7 @@ int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cu
         a.lgTL = ilog2(t.TL);
         a.TLP = t.L1 ? t.LP : t.TL + 1;
         a.coil_sum = coil_sum ? 1 : 0;
-        a.nchunks = 1;   // one channel chunk per block; chunks are blockIdx.y
+        a.nchunks = 1;   // one channel chunk per block
         const int chunks = (int)((S + t.TS - 1) / t.TS);
         a.in = in;
         a.out = out;
@@ -866,7 +870,7 @@ int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cu
         a.magic_L = magic_of((uint32_t)L);
         a.magic_n = magic_of((uint32_t)a.n_out);
         a.ntiles_s = chunks;
-        dim3 grid((unsigned)(((B + t.TB - 1) / t.TB) * chunks));
+        const dim3 grid = line_grid((B + t.TB - 1) / t.TB, chunks);
         const PassKind kind = last ? PASS_INV_LAST : PASS_INV_MID;
         st = launch(p, last ? PK_FFT_INV_LAST : PK_FFT_INV_MID, s, [&] {
             return t.L1 ? launch_line_pass2(kind, t.L1, t.L2, a, grid, t.threads, t.smem, s)
@@ -961,15 +965,22 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
         if (cudaMalloc(&p->d_deap[d], dp.size() * sizeof(float)) != cudaSuccess) return oom("scaling table");
         cudaMemcpy(p->d_deap[d], dp.data(), dp.size() * sizeof(float), cudaMemcpyHostToDevice);
         const int L = (int)p->K[d];
-        std::vector<float2> tw(L);
-        for (int t = 0; t < L; ++t) {
+        int L1 = 0, L2 = 0;
+        const bool two = fft2_factor(L, L1, L2);
+        std::vector<float2> tw(2 * (size_t)L);
+        auto unit = [&](int t) {
             const double ang = -2.0 * M_PI * (double)t / (double)L;
-            tw[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-        }
-        if (cudaMalloc(&p->d_tw[d], L * sizeof(float2)) != cudaSuccess) return oom("twiddles");
-        cudaMemcpy(p->d_tw[d], tw.data(), L * sizeof(float2), cudaMemcpyHostToDevice);
+            return make_float2((float)std::cos(ang), (float)std::sin(ang));
+        };
+        for (int t = 0; t < L; ++t) tw[t] = unit(t);
+        if (two)   // [n2][k1]: a thread's L1 - 1 twiddles sit at fixed offsets from its row
+            for (int n2 = 0; n2 < L2; ++n2)
+                for (int k1 = 0; k1 < L1; ++k1) tw[L + (size_t)n2 * L1 + k1] = unit(n2 * k1);
+        if (cudaMalloc(&p->d_tw[d], tw.size() * sizeof(float2)) != cudaSuccess) return oom("twiddles");
+        cudaMemcpy(p->d_tw[d], tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
         build_fft_axis(L, p->axis[d]);
         p->axis[d].tw = p->d_tw[d];
+        p->axis[d].tw2 = p->d_tw[d] + L;
     }
     if (cudaMalloc(&p->d_kcount, sizeof(int) * sort_keys(*p)) != cudaSuccess ||
         cudaMalloc(&p->d_offsets, sizeof(int) * (sort_keys(*p) + 1)) != cudaSuccess ||
@@ -1226,7 +1237,7 @@ int noalloc_scratch(void** out) {
 // Scaling factors s[n] = 1 / psi_hat((n - N/2) / K) (the Kaiser-Bessel transform in closed form, FP64)
 // and twiddles exp(-2 pi i t / L) of one axis, written into the scratch array on the device, so that
 // the call copies nothing from host memory.
-__global__ void k_noalloc_tables(float* deap, int64_t N, int64_t K, int J, double beta, float2* tw, int L) {
+__global__ void k_noalloc_tables(float* deap, int64_t N, int64_t K, int J, double beta, float2* tw, int L, int L1) {
     pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) {
@@ -1242,6 +1253,11 @@ __global__ void k_noalloc_tables(float* deap, int64_t N, int64_t K, int J, doubl
         double sn, cs;
         sincospi(-2.0 * (double)i / (double)L, &sn, &cs);
         tw[i] = make_float2((float)cs, (float)sn);
+        if (L1 > 0) {   // the two-phase table [n2][k1] = exp(-2 pi i n2 k1 / L), behind the linear one
+            const int n2 = (int)i / L1, k1 = (int)i - n2 * L1;
+            sincospi(-2.0 * (double)(n2 * k1) / (double)L, &sn, &cs);
+            tw[L + i] = make_float2((float)cs, (float)sn);
+        }
     }
 }
 
@@ -1266,7 +1282,7 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
     p.strip = false;   // forward only: the bin sort without the adjoint's strip tables
     p.wd = p.J;
     p.ws = (p.D * p.J + 3) & ~3;
-    if (C < 1 || C > 128) return fail(NUFFT_ERR_INVALID_ARG, "C must lie in [1, 128]");
+    if (C < 1 || C > NUFFT_MAX_COILS) return fail(NUFFT_ERR_INVALID_ARG, "C must lie in [1, 128]");
     if (m < 0 || m > (int64_t)INT32_MAX) return fail(NUFFT_ERR_INVALID_ARG, "m out of range");
     if (m > 0 && (!omega || !x || !y)) return fail(NUFFT_ERR_INVALID_ARG, "omega, x or y is NULL");
     p.maxC = C;
@@ -1284,7 +1300,7 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
     size_t o_deap[3], o_tw[3];
     for (int d = 0; d < p.D; ++d) {
         o_deap[d] = cv.take<float>(p.N[d]);
-        o_tw[d] = cv.take<float2>(p.K[d]);
+        o_tw[d] = cv.take<float2>(2 * p.K[d]);
     }
     const size_t o_kcount = cv.take<int>(p.nbins),
                  o_offsets = cv.take<int>(p.nbins + 1),
@@ -1309,11 +1325,14 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
         const int L = (int)p.K[d];
         p.d_deap[d] = (float*)(b + o_deap[d]);
         p.d_tw[d] = (float2*)(b + o_tw[d]);
+        int L1 = 0, L2 = 0;
+        if (!fft2_factor(L, L1, L2)) L1 = 0;
         const int64_t n = std::max<int64_t>(p.N[d], L);
         NJ_CUDA(launch_pdl(k_noalloc_tables, (unsigned)((n + 255) / 256), 256, 0, s, p.d_deap[d], p.N[d], p.K[d], p.J,
-                           p.beta, p.d_tw[d], L));
+                           p.beta, p.d_tw[d], L, L1));
         build_fft_axis(L, p.axis[d]);
         p.axis[d].tw = p.d_tw[d];
+        p.axis[d].tw2 = p.d_tw[d] + L;
     }
     p.d_kcount = (int*)(b + o_kcount);
     p.d_offsets = (int*)(b + o_offsets);

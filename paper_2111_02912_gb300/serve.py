@@ -8,13 +8,23 @@ Request kinds (2-D, SENSE model E = (I kron A) S, Sec. II-B, II-G):
 
 Scheduling: requests wait in FIFO order and are admitted as soon as an
 execution slot (a CUDA stream) is free and their device memory fits the budget
-(plan workspace from nufft_workspace_bytes plus the request's tensors).  Plans
-stay resident, pooled by (shape, coils, point capacity), and are reused by
-later requests (nufft_set_points re-sorts their bins).  An admitted request
-enqueues all its GPU work on its slot's stream without synchronising the host
-(the CG scalars stay on the device), so requests that arrive while others run
-overlap on the GPU.  Completion is detected by polling a CUDA event; latency is
-arrival to completion on the host clock.
+(plan workspace from nufft_workspace_bytes plus the request's tensors and CG
+temporaries).  Plans stay resident, pooled by (shape, channels, point capacity),
+and are reused by later requests (nufft_set_points re-sorts their bins).  An
+admitted job enqueues all its GPU work on its slot's stream without
+synchronising the host (the CG scalars stay on the device), so requests that
+arrive while others run overlap on the GPU.
+
+Fusion: reconstruction requests on the same problem (the same trajectory and
+maps, lam and iteration count) that are pending together are admitted as one
+job of up to ``fuse`` right-hand sides: one batched CG whose NUFFT calls carry
+all their coil images as channels of one plan (the kernels' per-point weights
+and sorted bins are then shared by the whole batch), with the CG scalars kept
+per request.
+
+Completion is detected by polling a CUDA event; latency is arrival to
+completion on the host clock, split into the wait before admission and the
+execution after it.
 """
 import collections
 import time
@@ -28,21 +38,23 @@ from .plan import Plan
 
 
 class Request:
-    __slots__ = ("rid", "kind", "shape", "omega", "x", "smaps", "y", "lam", "iters", "arrival", "done_at",
-                 "result", "bytes", "plan", "event", "slot")
+    __slots__ = ("rid", "kind", "shape", "omega", "x", "smaps", "y", "lam", "iters", "arrival", "admitted_at",
+                 "done_at", "result", "bytes", "plan", "event", "slot", "batch")
 
     def __init__(self, rid, kind, shape, omega, smaps, x=None, y=None, lam=1e-3, iters=15):
         self.rid, self.kind, self.shape = rid, kind, tuple(shape)
         self.omega, self.smaps, self.x, self.y = omega, smaps, x, y
         self.lam, self.iters = float(lam), int(iters)
-        self.arrival = self.done_at = None
+        self.arrival = self.admitted_at = self.done_at = None
         self.result = self.plan = self.event = self.slot = None
         self.bytes = 0
+        self.batch = 1   # requests in its job
 
 
 class Server:
-    def __init__(self, budget_bytes=120 << 30, slots=8, device="cuda"):
+    def __init__(self, budget_bytes=120 << 30, slots=8, device="cuda", fuse=8):
         self.device = torch.device(device)
+        self.fuse = max(1, int(fuse))
         self.budget = int(budget_bytes)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
         self.free_slots = list(range(slots))
@@ -71,44 +83,83 @@ class Server:
         return self.done
 
     # ---------------------------------------------------------------- internals
-    @staticmethod
-    def _key(req):
-        M = int(req.omega.shape[1])
-        C = int(req.smaps.shape[0])
-        return (req.shape, C, 1 << max(0, M - 1).bit_length())
+    def _fuse_limit(self, req):
+        """Most right-hand sides of one fused job: fuse, and no more coil images than one call takes."""
+        return max(1, min(self.fuse, _abi.NUFFT_MAX_COILS // int(req.smaps.shape[0])))
 
-    def _estimate(self, req, need_plan):
+    def _channels(self, req, batch):
+        """Channel capacity of the plan a job runs on: its coils, or for a fused job coils x the fuse
+        limit (one resident plan then serves fused jobs of every size)."""
+        C = int(req.smaps.shape[0])
+        return C if batch == 1 else C * self._fuse_limit(req)
+
+    def _key(self, req, batch=1):
+        M = int(req.omega.shape[1])
+        return (req.shape, self._channels(req, batch), 1 << max(0, M - 1).bit_length())
+
+    @staticmethod
+    def _same_problem(a, b):
+        return (a.kind == b.kind == "recon" and a.shape == b.shape and a.omega is b.omega and a.smaps is b.smaps
+                and a.lam == b.lam and a.iters == b.iters)
+
+    def _estimate(self, req, need_plan, batch=1):
+        """Device bytes of a job: its plan (if a new one is needed) and its tensors.  A reconstruction
+        keeps y, b = E'y and the CG vectors x, r, p, F p plus one forward output per right-hand side (a
+        fused one also the coil images S x and E'E p of every right-hand side); a trajectory gradient
+        keeps y, E x, v and grad_omega."""
         C, M, N = int(req.smaps.shape[0]), int(req.omega.shape[1]), int(np.prod(req.shape))
-        tensors = 8 * (C * M * 3 + N * 8)             # y / residual / forward output, CG vectors
+        D = len(req.shape)
+        if req.kind == "recon":
+            tensors = 8 * batch * (2 * C * M + 6 * N + (2 * C * N if batch > 1 else 0))
+        else:
+            tensors = 8 * (3 * C * M + N) + 4 * D * M
         if not need_plan:
             return tensors
         o = _abi.nufft_default_opts(len(req.shape), req.shape)
-        o.max_coils = C
+        o.max_coils = self._channels(req, batch)
         return tensors + _abi.nufft_workspace_bytes(o, self._key(req)[2])
 
     def _admit(self):
         while self.pending and self.free_slots:
             req = self.pending[0]
-            key = self._key(req)
+            # requests on the same problem waiting behind it join its job (FIFO order kept)
+            group = [req]
+            limit = self._fuse_limit(req) if req.kind == "recon" else 1
+            if limit > 1:
+                for other in list(self.pending)[1:]:
+                    if len(group) == limit:
+                        break
+                    if self._same_problem(req, other):
+                        group.append(other)
+            batch = len(group)
+            key = self._key(req, batch)
             idle = self.pool.get(key)
             need_plan = not idle
-            est = self._estimate(req, need_plan)
+            est = self._estimate(req, need_plan, batch)
             if need_plan and self.in_use + est > self.budget:
                 self._evict(est)
             if self.in_use + est > self.budget and self.running:
                 return                                  # wait for memory (FIFO: no overtaking)
-            self.pending.popleft()
+            for r in group:
+                self.pending.remove(r)
             slot = self.free_slots.pop()
+            now = time.perf_counter()
             with torch.cuda.stream(self.streams[slot]):
                 if need_plan:
-                    plan = Plan(req.shape, req.omega, max_coils=int(req.smaps.shape[0]))
-                    self.plan_bytes[id(plan)] = est - self._estimate(req, False)
+                    plan = Plan(req.shape, req.omega, max_coils=self._channels(req, batch))
+                    self.plan_bytes[id(plan)] = est - self._estimate(req, False, batch)
                 else:
                     plan = idle.pop()
-                req.plan, req.slot, req.bytes = plan, slot, self._estimate(req, False)
-                self.in_use += req.bytes + (self.plan_bytes[id(plan)] if need_plan else 0)
-                self._launch(req)
-            self.running.append(req)
+                job_bytes = self._estimate(req, False, batch)
+                self.in_use += job_bytes + (self.plan_bytes[id(plan)] if need_plan else 0)
+                for r in group:
+                    r.plan, r.slot, r.bytes, r.batch, r.admitted_at = plan, slot, 0, batch, now
+                req.bytes = job_bytes
+                if batch == 1:
+                    self._launch(req)
+                else:
+                    self._launch_fused(group)
+            self.running.append(group)
 
     def _evict(self, need):
         for key in list(self.pool):
@@ -132,22 +183,71 @@ class Server:
         req.event = torch.cuda.Event()
         req.event.record(self.streams[req.slot])
 
+    def _launch_fused(self, group):
+        """One CG for B right-hand sides on one problem: E and E' act on all B x C coil images at once
+        (maps applied around the channel-batched calls), every scalar per request."""
+        req0 = group[0]
+        plan, S = req0.plan, req0.smaps
+        B, C = len(group), int(S.shape[0])
+        plan.set_points(req0.omega)
+        conjS = S.conj()
+
+        def E(X):    # [B][N...] -> [B C][M]
+            return plan.forward((S.unsqueeze(0) * X.unsqueeze(1)).reshape((B * C,) + req0.shape))
+
+        def Eh(Y):   # [B C][M] -> [B][N...]
+            coil = plan.adjoint(Y).reshape((B, C) + req0.shape)
+            return (conjS.unsqueeze(0) * coil).sum(dim=1)
+
+        dims = tuple(range(1, 1 + len(req0.shape)))
+        vdot = lambda a, b: (a.conj() * b).sum(dim=dims).real.reshape((B,) + (1,) * len(dims))
+        Y = torch.cat([r.y for r in group], dim=0)
+        bvec = Eh(Y)
+        x = torch.zeros_like(bvec)
+        r = bvec.clone()
+        p = r.clone()
+        rr = vdot(r, r)
+        for _ in range(req0.iters):
+            Fp = Eh(E(p)) + req0.lam * p
+            alpha = rr / vdot(p, Fp)
+            x = x + alpha * p
+            r = r - alpha * Fp
+            rr_new = vdot(r, r)
+            p = r + (rr_new / rr) * p
+            rr = rr_new
+        ev = torch.cuda.Event()
+        ev.record(self.streams[req0.slot])
+        for b, rq in enumerate(group):
+            rq.result = x[b]
+            rq.event = ev
+
     def _retire(self):
         still = []
-        for req in self.running:
+        for group in self.running:
+            req = group[0]
             if req.event.query():
-                req.done_at = time.perf_counter()
+                now = time.perf_counter()
                 self.free_slots.append(req.slot)
                 self.in_use -= req.bytes
-                self.pool[self._key(req)].append(req.plan)
-                req.plan = None
-                self.done.append(req)
+                self.pool[self._key(req, len(group))].append(req.plan)
+                for r in group:
+                    r.done_at = now
+                    r.plan = None
+                    self.done.append(r)
             else:
-                still.append(req)
+                still.append(group)
         self.running = still
 
 
 def latency_summary(done):
+    """Arrival-to-completion latency, and its two phases: the wait before admission and the execution
+    after it (a request in a fused job shares its job's execution)."""
     lat = np.array([(r.done_at - r.arrival) * 1e3 for r in done])
+    wait = np.array([(r.admitted_at - r.arrival) * 1e3 for r in done])
+    run = lat - wait
+    batch = np.array([r.batch for r in done])
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "n": int(lat.size)}
+            "mean_ms": float(lat.mean()), "n": int(lat.size),
+            "wait_p50_ms": float(np.percentile(wait, 50)), "wait_p99_ms": float(np.percentile(wait, 99)),
+            "exec_p50_ms": float(np.percentile(run, 50)), "exec_p99_ms": float(np.percentile(run, 99)),
+            "fused_requests": int((batch > 1).sum()), "mean_job_size": float(batch.mean())}

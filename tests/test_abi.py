@@ -50,6 +50,18 @@ def test_struct_layout_matches_c(abi, tmp_path):
     assert got == want
 
 
+def test_header_constants_match_the_binding(abi, tmp_path):
+    src = tmp_path / "consts.c"
+    src.write_text('#include <stdio.h>\n#include "nufftjac.h"\n'
+                   'int main(void){printf("%d %u %d %d\\n", NUFFT_MAX_COILS, NUFFT_NOALLOC_SCRATCH_BYTES,'
+                   ' NUFFT_SPREAD_STRIPS, NUFFT_ERR_TIMEOUT); return 0;}\n')
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    want = [abi.NUFFT_MAX_COILS, abi.NUFFT_NOALLOC_SCRATCH_BYTES, abi.NUFFT_SPREAD_STRIPS, abi.NUFFT_ERR_TIMEOUT]
+    assert got == want
+
+
 def test_default_opts_and_status_strings(abi):
     o = abi.nufft_default_opts(2, (320, 320))
     assert (o.dim, o.n[0], o.n[1], o.J, o.sigma, o.max_coils) == (2, 320, 320, 6, 2.0, 1)
@@ -62,7 +74,7 @@ def test_default_opts_and_status_strings(abi):
     (lambda o: o.n.__setitem__(0, 63), -2),
     (lambda o: setattr(o, "J", 9), -2),
     (lambda o: setattr(o, "sigma", 0.9), -2),
-    (lambda o: setattr(o, "max_coils", 129), -2),
+    (lambda o: setattr(o, "max_coils", 129), -2),   # NUFFT_MAX_COILS + 1
     (lambda o: o.n.__setitem__(0, 2), -2),          # K = 4 < J = 6
     (lambda o: o.n.__setitem__(1, 4000), -2),       # K = 8000 > 4096
 ])

@@ -89,3 +89,40 @@ def test_admission_waits_for_memory_and_reuses_plans():
         srv2.submit(r)
     srv2.drain()
     assert sum(len(v) for v in srv2.pool.values()) == n_plans     # resident plans reused
+
+
+def test_same_problem_requests_fuse_into_one_job():
+    """Four reconstructions on one trajectory and one set of maps, pending together: one job of four
+    right-hand sides, each result the same as alone and as the FP64 CG."""
+    import torch
+
+    from paper_2111_02912_gb300.serve import Request, Server, latency_summary
+    p, _ = _requests()[2]
+    om, S = to_dev(p["omega"]), to_dev(p["smaps"])
+    g = np.random.default_rng(61)
+    ys = [g.standard_normal(p["v"].shape) + 1j * g.standard_normal(p["v"].shape) for _ in range(4)]
+    lam = 10.0 * p["omega"].shape[1]
+    mk = lambda i: Request(i, "recon", p["shape"], om, S, y=to_dev(ys[i].astype(np.complex64)), lam=lam, iters=15)
+    alone = []
+    for i in range(4):
+        srv = Server(budget_bytes=8 << 30, slots=2, fuse=1)
+        r = mk(i)
+        srv.submit(r)
+        srv.drain()
+        torch.cuda.synchronize()
+        assert r.batch == 1
+        alone.append(host(r.result).copy())
+    srv = Server(budget_bytes=8 << 30, slots=2, fuse=8)
+    reqs = [mk(i) for i in range(4)]
+    for r in reqs:
+        srv.submit(r)
+    done = srv.drain()
+    torch.cuda.synchronize()
+    assert len(done) == 4 and all(r.batch == 4 for r in reqs)
+    for i, r in enumerate(reqs):
+        assert rel(host(r.result), alone[i]) < 1e-5
+        pi = dict(p, v=ys[i])
+        assert rel(host(r.result), _oracle(pi, r)) < 1e-4
+    s = latency_summary(done)
+    assert s["fused_requests"] == 4 and s["mean_job_size"] == 4.0
+    assert s["wait_p50_ms"] >= 0 and s["exec_p50_ms"] > 0
