@@ -53,6 +53,8 @@ def parse():
                     help="radial320: adjoint spread kernel (auto: the library's choice, register strips in 2-D)")
     ap.add_argument("--serve-problems", type=int, default=64,
                     help="serving: distinct problems (trajectory + maps) the requests draw from")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: offered requests per second")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving: length of the arrival process")
     ap.add_argument("--serve-fuse", type=int, default=8,
                     help="serving: most same-problem reconstructions fused into one job (1: no fusion)")
     ap.add_argument("--no-graph", action="store_true",
@@ -678,7 +680,7 @@ def run_batched(args):
 
 
 # ------------------------------------------------------------------ serving
-def run_serving(args, rate=200.0, seconds=3.0):
+def run_serving(args):
     import torch
 
     from paper_2111_02912_gb300.serve import Request, Server, latency_summary
@@ -690,6 +692,7 @@ def run_serving(args, rate=200.0, seconds=3.0):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     pool = [dict(shape=p["shape"], om=t(p["omega"]), S=t(p["smaps"]), x=t(p["x"]), y=t(p["v"]), C=p["C"],
                  M=p["omega"].shape[1]) for p in probs]
+    rate, seconds = args.serve_rate, args.serve_seconds
     g = np.random.default_rng(2111_02912 + 5)
     n_req = int(rate * seconds)
     arrivals = np.cumsum(g.exponential(1.0 / rate, n_req))

@@ -54,11 +54,24 @@ __device__ __forceinline__ void image_row_factors(const ImageSide& im, int64_t b
 // 22.4 us against 128 registers at two blocks per SM).  Other sizes keep 128: on the 400-point
 // passes (320-thread blocks) 80 registers cost FWD_FIRST 24.5 -> 28.3 us and FWD_MID 17.3 -> 19.0
 // us.  The coil-summing INV_LAST runs 512-thread blocks and keeps 128 as well.
+// Half-length pruning fixed at compile time (HALF: n_in = L / 2 on the forward side, n_out = L / 2 on
+// the inverse side, i.e. sigma = 2).  Then the kept positions p < L/4 or p >= 3L/4 are whole phase-1
+// registers n1 (p = L2 n1 + n2, L1 % 4 == 0) on the forward side and whole phase-2 outputs k2
+// (k = k1 + L1 k2, L2 % 4 == 0) on the inverse side: the zero inputs are never loaded and the
+// dropped outputs never computed.
 template <int L1, int L2, PassKind KIND>
+__host__ __device__ constexpr bool fft2_half_applies() {
+    return (KIND == PASS_FWD_FIRST || KIND == PASS_FWD_MID) ? L1 % 4 == 0 : L2 % 4 == 0;
+}
+
+template <int L1, int L2, PassKind KIND, bool HALF>
 __global__ void __maxnreg__((KIND == PASS_INV_LAST || L2 != 32) ? 128 : 80) k_line_fft2(LinePass a) {
     pdl_wait();
     constexpr int DIR = (KIND == PASS_FWD_FIRST || KIND == PASS_FWD_MID) ? -1 : 1;
     constexpr int L = L1 * L2;
+    constexpr bool FH = HALF && DIR < 0 && fft2_half_applies<L1, L2, KIND>();   // forward: n1 kept iff
+    constexpr bool IH = HALF && DIR > 0 && fft2_half_applies<L1, L2, KIND>();   // inverse: k2 kept iff
+    constexpr int Q = L / 4;
     constexpr int RP = L2 + 1;   // row pitch inside a line
     const int LP = a.TLP;        // line pitch (>= L1 RP, >= n_out)
     extern __shared__ float2 buf[];   // [TL][LP]
@@ -106,7 +119,8 @@ __global__ void __maxnreg__((KIND == PASS_INV_LAST || L2 != 32) ? 128 : 80) k_li
                 }
             }
             float2* dst = buf + ln * LP;
-            for (int p = h + lane; p < L - h; p += 32) dst[p + p / L2] = make_float2(0.f, 0.f);   // zero padding
+            if (!FH)   // zero padding (with FH the padded registers are never read)
+                for (int p = h + lane; p < L - h; p += 32) dst[p + p / L2] = make_float2(0.f, 0.f);
             // image element e sits at position (e - n_in/2) mod L.  A row of up to 384
             // elements is loaded in one batch of 12 per lane; indices are clamped so the
             // loads are unconditional and independent (all in flight before the first use).
@@ -156,7 +170,21 @@ __global__ void __maxnreg__((KIND == PASS_INV_LAST || L2 != 32) ? 128 : 80) k_li
         if (KIND == PASS_FWD_FIRST) {
             sfor<0, L1>([&](auto n1_) {
                 constexpr int n1 = decltype(n1_)::value;
-                v[n1] = row[n1 * RP + n2];
+                if constexpr (FH && n1 >= L1 / 4 && n1 < 3 * L1 / 4) v[n1] = make_float2(0.f, 0.f);
+                else v[n1] = row[n1 * RP + n2];
+            });
+        } else if constexpr (FH && KIND == PASS_FWD_MID) {
+            // kept rows: element e = p + L/4 for p < L/4, p - 3L/4 for p >= 3L/4 (n_in = L/2)
+            const float2* base = a.in + (valid ? b * a.n_in * S + sl : 0) + (int64_t)n2 * Si;
+            sfor<0, L1>([&](auto n1_) {
+                constexpr int n1 = decltype(n1_)::value;
+                if constexpr (n1 >= L1 / 4 && n1 < 3 * L1 / 4) {
+                    v[n1] = make_float2(0.f, 0.f);
+                } else {
+                    constexpr int e0 = n1 < L1 / 4 ? n1 * L2 + Q : n1 * L2 - 3 * Q;   // e - n2
+                    const float2 t = __ldg(base + (int64_t)e0 * Si);   // in bounds for every line
+                    v[n1] = valid ? t : make_float2(0.f, 0.f);
+                }
             });
         } else {
             const float2* in_line = a.in + (valid ? b * a.n_in * S + sl : 0);
@@ -220,9 +248,16 @@ __global__ void __maxnreg__((KIND == PASS_INV_LAST || L2 != 32) ? 128 : 80) k_li
             float2* out_line = a.out + b * a.n_out * S + sl;
             sfor<0, L2>([&](auto k2_) {
                 constexpr int k2 = decltype(k2_)::value;
-                const int k = k1 + L1 * k2;
-                const int e = k < h ? k + h : k - (L - h);
-                if (k < h || k >= L - h) out_line[(int64_t)e * Si] = w[k2];
+                if constexpr (IH) {   // kept: k2 < L2/4 (e = k + L/4) or k2 >= 3 L2/4 (e = k - 3L/4)
+                    if constexpr (k2 < L2 / 4 || k2 >= 3 * L2 / 4) {
+                        constexpr int c = k2 < L2 / 4 ? L1 * k2 + Q : L1 * k2 - 3 * Q;
+                        out_line[(int64_t)(k1 + c) * Si] = w[k2];
+                    }
+                } else {
+                    const int k = k1 + L1 * k2;
+                    const int e = k < h ? k + h : k - (L - h);
+                    if (k < h || k >= L - h) out_line[(int64_t)e * Si] = w[k2];
+                }
             });
         }
     } else {   // PASS_INV_LAST: crop into shared memory, then the image side
@@ -231,9 +266,16 @@ __global__ void __maxnreg__((KIND == PASS_INV_LAST || L2 != 32) ? 128 : 80) k_li
         if (k1 < L1) {
             sfor<0, L2>([&](auto k2_) {
                 constexpr int k2 = decltype(k2_)::value;
-                const int k = k1 + L1 * k2;
-                const int e = k < h ? k + h : k - (L - h);
-                if (k < h || k >= L - h) row[e] = w[k2];
+                if constexpr (IH) {
+                    if constexpr (k2 < L2 / 4 || k2 >= 3 * L2 / 4) {
+                        constexpr int c = k2 < L2 / 4 ? L1 * k2 + Q : L1 * k2 - 3 * Q;
+                        row[k1 + c] = w[k2];
+                    }
+                } else {
+                    const int k = k1 + L1 * k2;
+                    const int e = k < h ? k + h : k - (L - h);
+                    if (k < h || k >= L - h) row[e] = w[k2];
+                }
             });
         }
         __syncthreads();
@@ -282,11 +324,18 @@ namespace nj {
 // Launches k_line_fft2<L1, L2, KIND> when (L1, L2) has a compiled kernel.
 template <PassKind KIND>
 cudaError_t launch_fft2_kind(int L1, int L2, const LinePass& a, dim3 grid, int threads, size_t smem, cudaStream_t s) {
-#define NJ_FFT2_CASE(A, B)                                                  \
-    if (L1 == A && L2 == B) {                                                \
-        ensure_smem<k_line_fft2<A, B, KIND>>(smem);                          \
-        (void)launch_pdl(k_line_fft2<A, B, KIND>, grid, threads, smem, s, a);              \
-        return cudaGetLastError();                                           \
+#define NJ_FFT2_CASE(A, B)                                                                   \
+    if (L1 == A && L2 == B) {                                                                 \
+        if constexpr (fft2_half_applies<A, B, KIND>()) {                                      \
+            if (2 * ((KIND == PASS_FWD_FIRST || KIND == PASS_FWD_MID) ? a.n_in : a.n_out) == A * B) { \
+                ensure_smem<k_line_fft2<A, B, KIND, true>>(smem);                             \
+                (void)launch_pdl(k_line_fft2<A, B, KIND, true>, grid, threads, smem, s, a);   \
+                return cudaGetLastError();                                                    \
+            }                                                                                 \
+        }                                                                                     \
+        ensure_smem<k_line_fft2<A, B, KIND, false>>(smem);                                    \
+        (void)launch_pdl(k_line_fft2<A, B, KIND, false>, grid, threads, smem, s, a);          \
+        return cudaGetLastError();                                                            \
     }
     NJ_FFT2_SIZES(NJ_FFT2_CASE)
 #undef NJ_FFT2_CASE
