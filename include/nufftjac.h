@@ -84,14 +84,22 @@ typedef struct {
     int spread_variant; /* adjoint spread kernel: NUFFT_SPREAD_AUTO (0), _STRIPS, _TILES, _GENERAL */
     int strip_part;   /* strip spread: hits one warp adds before a unit is split into parts
                          (a power of two, 8..4096; 0 -> 64) */
+    int kernel_mode;  /* how the interpolation weights psi(u) are evaluated (once per omega, by the
+                         bin sort): NUFFT_KERNEL_DIRECT (0), the Kaiser-Bessel function itself as
+                         its I0 power series in FP32; NUFFT_KERNEL_TABLE, psi sampled at
+                         table_density points per grid unit and read by linear interpolation (the
+                         table interpolator of Sec. II-B / Sec. IV-A, for comparison; less accurate) */
+    int table_density; /* NUFFT_KERNEL_TABLE: samples per grid unit, 16..65536 (0 -> 512) */
     int reserved[1];
 } nufft_opts;
 
+enum { NUFFT_KERNEL_DIRECT = 0, NUFFT_KERNEL_TABLE = 1 };
+
 /* Adjoint spread kernels (nufft_opts.spread_variant), all computing the transpose of the
  * interpolation (Sec. II-D); AUTO takes STRIPS where it applies, else TILES, else GENERAL.
- *   STRIPS  2-D only: a warp owns NSL grid rows x 16 columns in registers (NSL = 32 / coils per
- *           warp, from max_coils); needs column bins of 16 (the default) and a grid of at
- *           least 16 + J - 1 columns and NSL + J - 1 rows.
+ *   STRIPS  2-D only: a warp owns NSL grid rows x 16 columns in registers (NSL = 64 / coils per
+ *           warp: 4 for 16 coils, from max_coils); needs a grid of at least 16 + J - 1 columns
+ *           and NSL + J - 1 rows.
  *   TILES   2-D / 3-D: a block owns one bin tile in shared memory (row or cell owners).
  *   GENERAL any D: shared-memory atomics on bin tiles.
  * Asking for a variant that does not apply to the plan returns NUFFT_ERR_UNSUPPORTED. */

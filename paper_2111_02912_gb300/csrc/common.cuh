@@ -32,6 +32,16 @@ __device__ __forceinline__ float kb_psi(const float* __restrict__ a, float two_o
     return z > 0.f ? acc : 0.f;
 }
 
+// psi read from a table of psi(l / L), l = 0 .. n + 1, zero from l = n = L J / 2 on, by linear
+// interpolation in |u| L: the table interpolator the paper's baseline uses (Sec. II-B, Sec. IV-A).
+__device__ __forceinline__ float kb_table(const float* __restrict__ tab, float L, int n, float u) {
+    const float au = fabsf(u) * L;
+    const float lf = floorf(au);
+    const int l = min((int)lf, n);
+    const float a = au - lf;
+    return fmaf(a, __ldg(tab + l + 1) - __ldg(tab + l), __ldg(tab + l));
+}
+
 // ---------------------------------------------------------- sorted points
 // Per point, per dim: wrapped window start k0 in [0, K) and the offset of the
 // first tap u0 = t - k0_unwrapped in [J/2 - 1, J/2); tap j has offset u0 - j.

@@ -98,6 +98,9 @@ struct SortArgs {
     float* pw;        // [M][ws]   kernel weights psi(u0_d - j) of the sorted points, at d * wd + j
     int ws, wd;
     KbPoly kb;
+    const float* kbtab;   // table mode: psi(l / tab_L) for l = 0 .. tab_n + 1 (zero from tab_n on), else null
+    float tab_L;
+    int tab_n;
     // 2-D strip mode: the scatter also counts the strip units' hits, then the plan and fill
     int strip, nunits;
     StripGeom sg;

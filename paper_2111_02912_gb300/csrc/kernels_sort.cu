@@ -267,7 +267,10 @@ __global__ void k_bin_scatter(SortArgs a) {
     float* w = a.pw + (int64_t)dst * a.ws;
     for (int d = 0; d < a.D; ++d) {
         const float u0 = d == 0 ? fr.x : (d == 1 ? fr.y : fr.z);
-        for (int j = 0; j < a.J; ++j) w[d * a.wd + j] = kb_psi(a.kb.a, a.kb.two_over_j, u0 - (float)j);
+        if (a.kbtab)
+            for (int j = 0; j < a.J; ++j) w[d * a.wd + j] = kb_table(a.kbtab, a.tab_L, a.tab_n, u0 - (float)j);
+        else
+            for (int j = 0; j < a.J; ++j) w[d * a.wd + j] = kb_psi(a.kb.a, a.kb.two_over_j, u0 - (float)j);
         for (int j = a.J; j < a.wd; ++j) w[d * a.wd + j] = 0.f;
     }
     // 2-D strips: count the point as a hit of every unit its window reaches

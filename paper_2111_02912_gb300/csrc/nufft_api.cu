@@ -88,6 +88,8 @@ struct nufft_plan_s {
     // 2-D strip spread: sort keys (bin, start row), strip units of NSL rows x kStripW columns
     bool strip = false;
     bool deterministic = false;    // stable bin order and hit lists ordered by sorted point
+    int kernel_mode = NUFFT_KERNEL_DIRECT, tab_L = 0, tab_n = 0;   // table mode: L samples per unit
+    float* d_kbtab = nullptr;      // [tab_n + 2] psi(l / tab_L), zero from tab_n on
     int2* d_hits_tmp = nullptr;    // [hit_cap] the fill's list before ordering (deterministic only)
     int NSL = 2, nunits = 0, strip_P = 64, strip_slots = 0, ncg_max = 1;
     float2* d_ys = nullptr;        // [ncg_max][M_cap][64 / NSL] coil values in sorted point order
@@ -198,6 +200,20 @@ void build_fft_axis(int L, FftAxis& ax) {
     }
 }
 
+// psi(u) = I0(beta sqrt(1 - (2u/J)^2)) for |u| < J/2, else 0, by the power series of I0 in FP64
+// (terms past 1e-17 of the sum dropped).
+double kb_psi_fp64(double u, int J, double beta) {
+    const double s = 2.0 * u / J, z = 1.0 - s * s;
+    if (z <= 0.0) return 0.0;
+    const double q = beta * beta / 4.0 * z;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 200 && term > 1e-17 * sum; ++k) {
+        term *= q / ((double)k * k);
+        sum += term;
+    }
+    return sum;
+}
+
 // Kaiser-Bessel Fourier transform int psi(u) exp(-2 pi i f u) du in closed form.
 double kb_ft(double f, int J, double beta) {
     const double a = beta * beta - (M_PI * J * f) * (M_PI * J * f);
@@ -208,6 +224,7 @@ double kb_ft(double f, int J, double beta) {
 
 void free_plan(nufft_plan_s* p) {
     for (int d = 0; d < 3; ++d) { cudaFree(p->d_deap[d]); cudaFree(p->d_tw[d]); }
+    cudaFree(p->d_kbtab);
     cudaFree(p->d_kcount); cudaFree(p->d_offsets); cudaFree(p->d_item_off); cudaFree(p->d_tile_parts); cudaFree(p->d_heavy); cudaFree(p->d_tile_nbr);
     cudaFree(p->d_nitems); cudaFree(p->d_items); cudaFree(p->d_local); cudaFree(p->d_keyid); cudaFree(p->d_pidx); cudaFree(p->d_pfrac);
     cudaFree(p->d_pw); cudaFree(p->d_om);
@@ -320,6 +337,14 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
     }
     if (ak > 1e-9 * sum) return fail(NUFFT_ERR_UNSUPPORTED, "beta too large for the kernel power series");
     p.kb.two_over_j = (float)(2.0 / p.J);
+    p.kernel_mode = o->kernel_mode;
+    if (p.kernel_mode != NUFFT_KERNEL_DIRECT && p.kernel_mode != NUFFT_KERNEL_TABLE)
+        return fail(NUFFT_ERR_INVALID_ARG, "kernel_mode must be NUFFT_KERNEL_DIRECT or NUFFT_KERNEL_TABLE");
+    if (p.kernel_mode == NUFFT_KERNEL_TABLE) {
+        p.tab_L = o->table_density ? o->table_density : 512;
+        if (p.tab_L < 16 || p.tab_L > 65536) return fail(NUFFT_ERR_INVALID_ARG, "table_density must lie in [16, 65536]");
+        p.tab_n = p.tab_L * p.J / 2;
+    }
     p.wd = p.strip ? 8 : p.J;   // the strip spread reads the column weights as two 16-byte loads
     p.ws = p.strip ? 16 : (p.D * p.J + 3) & ~3;
     for (int d = 0; d < p.D; ++d) {
@@ -483,6 +508,9 @@ SortArgs sort_args(nufft_plan_s* p, const float* omega) {
     a.ws = p->ws;
     a.wd = p->wd;
     a.kb = p->kb;
+    a.kbtab = p->d_kbtab;
+    a.tab_L = (float)p->tab_L;
+    a.tab_n = p->tab_n;
     a.strip = p->strip ? 1 : 0;
     a.nunits = p->nunits;
     a.sg = strip_geom(*p);
@@ -941,7 +969,8 @@ size_t nufft_workspace_bytes(const nufft_opts* o, int64_t m, int C) {
     workspace_elems(p, G, T);
     size_t b = (G + T) * sizeof(float2) + point_bytes(p, std::max<int64_t>(m, 1));
     b += (size_t)((4 + kNbrStride) * p.nbins + 2 * sort_keys(p) + 8) * sizeof(int) + strip_bytes(p);
-    for (int d = 0; d < p.D; ++d) b += (size_t)p.N[d] * sizeof(float) + (size_t)p.K[d] * sizeof(float2);
+    for (int d = 0; d < p.D; ++d) b += (size_t)p.N[d] * sizeof(float) + 2 * (size_t)p.K[d] * sizeof(float2);
+    if (p.kernel_mode == NUFFT_KERNEL_TABLE) b += (size_t)(p.tab_n + 2) * sizeof(float);
     return b;
 }
 
@@ -981,6 +1010,13 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
         build_fft_axis(L, p->axis[d]);
         p->axis[d].tw = p->d_tw[d];
         p->axis[d].tw2 = p->d_tw[d] + L;
+    }
+    if (p->kernel_mode == NUFFT_KERNEL_TABLE) {
+        // psi(l / L) for l = 0 .. n + 1 from the FP64 power series, zero from l = n = L J / 2 on
+        std::vector<float> tab(p->tab_n + 2, 0.f);
+        for (int l = 0; l < p->tab_n; ++l) tab[l] = (float)kb_psi_fp64((double)l / p->tab_L, p->J, p->beta);
+        if (cudaMalloc(&p->d_kbtab, tab.size() * sizeof(float)) != cudaSuccess) return oom("kernel table");
+        cudaMemcpy(p->d_kbtab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
     if (cudaMalloc(&p->d_kcount, sizeof(int) * sort_keys(*p)) != cudaSuccess ||
         cudaMalloc(&p->d_offsets, sizeof(int) * (sort_keys(*p) + 1)) != cudaSuccess ||
@@ -1280,6 +1316,8 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
     int st = validate_opts(o, p);
     if (st) return st;
     p.strip = false;   // forward only: the bin sort without the adjoint's strip tables
+    if (p.kernel_mode != NUFFT_KERNEL_DIRECT)
+        return fail(NUFFT_ERR_UNSUPPORTED, "nufft_forward_noalloc evaluates the kernel directly only");
     p.wd = p.J;
     p.ws = (p.D * p.J + 3) & ~3;
     if (C < 1 || C > NUFFT_MAX_COILS) return fail(NUFFT_ERR_INVALID_ARG, "C must lie in [1, 128]");

@@ -106,3 +106,22 @@ def test_workspace_bytes_scale_with_coils_and_grid(abi):
     o.max_coils = 1
     assert abi.nufft_workspace_bytes(o, 51200) < b16 / 8
     assert abi.nufft_workspace_bytes(o, 51200, 16) == b16      # C overrides max_coils
+
+
+@pytest.mark.parametrize("mode,density", [(2, 0), (-1, 0), (1, 8), (1, 70000)])
+def test_invalid_kernel_mode_or_table_density_is_rejected(abi, mode, density):
+    o = abi.nufft_default_opts(2, (64, 64))
+    o.kernel_mode = mode
+    o.table_density = density
+    with pytest.raises(abi.NufftError) as e:
+        abi.nufft_plan(o, 0, None)
+    assert e.value.status == abi.NUFFT_ERR_INVALID_ARG
+    assert abi.nufft_workspace_bytes(o, 100, 0) == 0
+
+
+def test_table_mode_workspace_counts_the_table(abi):
+    o = abi.nufft_default_opts(2, (64, 64))
+    direct = abi.nufft_workspace_bytes(o, 1000, 1)
+    o.kernel_mode = abi.NUFFT_KERNEL_TABLE
+    o.table_density = 1024
+    assert abi.nufft_workspace_bytes(o, 1000, 1) == direct + (1024 * 6 // 2 + 2) * 4

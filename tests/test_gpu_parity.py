@@ -9,6 +9,7 @@ import pytest
 from gpu_helpers import host, make_case, max_rel, rel, to_dev
 from oracle import jacobian as jb
 from oracle.nudft import NUDFT
+from oracle.naive import TableNufft
 from oracle.nufft import KBNufft
 
 pytestmark = pytest.mark.gpu
@@ -99,7 +100,7 @@ def test_all_products_match_same_kernel_oracle(name, shape, M, C, maps, opts):
     assert max_rel(host(gx), gx_ref) < TOL_SAME
 
 
-# The 2-D strip spread: every coils-per-warp width (32 / NSL coils for NSL rows), J 4..8, grids
+# The 2-D strip spread: every coils-per-warp width (64 / NSL coils for NSL rows), J 4..8, grids
 # just wide enough for it (K1 = 16 + J - 1 columns, K0 = NSL + J - 1 rows: windows wrap around both
 # axes), several coil groups, and the two other spread kernels on the same problem.
 STRIP_CASES = [
@@ -353,4 +354,59 @@ def test_deterministic_refused_without_the_strip_spread():
     case = make_case((8, 10, 6), 100, 2, True, seed=2)
     with pytest.raises(_abi.NufftError) as e:
         _plan(case, deterministic=True)
+    assert e.value.status == _abi.NUFFT_ERR_UNSUPPORTED
+
+
+# Interpolation weights read from a linearly interpolated table of psi (nufft_opts.kernel_mode =
+# NUFFT_KERNEL_TABLE): every product against the oracle's table NUFFT of the same density.
+TABLE_CASES = [
+    # name, shape, M, C, maps, opts, L
+    ("table_1d", (64,), 700, 2, True, {}, 512),
+    ("table_2d_strips", (32, 40), 1500, 3, True, {}, 512),
+    ("table_2d_strips_L64", (32, 40), 1500, 3, True, {}, 64),
+    ("table_2d_tiles", (32, 40), 1500, 3, True, dict(spread="tiles"), 256),
+    ("table_2d_low_accuracy", (40, 48), 1200, 2, True, dict(J=5, sigma=1.25), 1024),
+    ("table_3d", (16, 20, 12), 2000, 2, True, {}, 512),
+]
+
+
+@pytest.mark.parametrize("name,shape,M,C,maps,opts,L", TABLE_CASES, ids=[c[0] for c in TABLE_CASES])
+def test_table_kernel_mode_matches_oracle_table_nufft(name, shape, M, C, maps, opts, L):
+    import torch
+    seed = sum(map(ord, name))
+    case = make_case(shape, M, C, maps, seed=seed)
+    plan = _plan(case, kernel_mode="table", table_density=L, **opts)
+    X, S, V, Y, DOM = (to_dev(case[k]) for k in ("x", "smaps", "v", "y", "domega"))
+    y = plan.forward(X, S)
+    xa = plan.adjoint(Y, S)
+    dy = plan.jvp_omega(X, DOM, S)
+    go, gx = plan.vjp_omega_x(X, V, S)
+    torch.cuda.synchronize()
+    kw = {k: v for k, v in opts.items() if k in ("J", "sigma")}
+    op = TableNufft(shape, case["omega"], L=L, **kw)
+    s = case["smaps"]
+    y_ref = jb.sense_forward(op, case["x"], s)
+    assert rel(host(y), y_ref) < TOL_SAME
+    xa_ref = jb.sense_adjoint(op, case["y"], s)
+    assert rel(host(xa), xa_ref) < TOL_SAME and max_rel(host(xa), xa_ref) < TOL_SAME
+    assert rel(host(dy), jb.jvp_omega(op, case["x"], case["domega"], s)) < TOL_SAME
+    go_ref, gx_ref = jb.vjp_omega_x(op, case["x"], case["v"], s)
+    assert rel(host(go), go_ref) < TOL_SAME
+    assert rel(host(gx), gx_ref) < TOL_SAME and max_rel(host(gx), gx_ref) < TOL_SAME
+    # the table differs from the kernel itself by its interpolation error (O(1 / L^2) inside the
+    # support, plus the ramp over the last 1 / L to the zero beyond |u| = J / 2)
+    y_direct = jb.sense_forward(KBNufft(shape, case["omega"], **kw), case["x"], s)
+    assert 0.0 < rel(y_ref, y_direct) < 1e-4
+
+
+def test_kernel_mode_refused_by_the_allocation_free_forward():
+    from paper_2111_02912_gb300 import _abi
+    case = make_case((16, 16), 100, 1, False, seed=3)
+    o = _abi.nufft_default_opts(2, (16, 16))
+    o.kernel_mode = _abi.NUFFT_KERNEL_TABLE
+    om, x = to_dev(case["omega"]), to_dev(case["x"])
+    import torch
+    y = torch.empty((1, 100), dtype=torch.complex64, device="cuda")
+    with pytest.raises(_abi.NufftError) as e:
+        _abi.nufft_forward_noalloc(o, 100, om.data_ptr(), 1, x.data_ptr(), 0, y.data_ptr(), 0)
     assert e.value.status == _abi.NUFFT_ERR_UNSUPPORTED
