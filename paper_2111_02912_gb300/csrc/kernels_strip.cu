@@ -279,9 +279,10 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Staging rows are XOR-swizzled by the hit index in 16-byte chunks, so that the asynchronous copies
-// of eight lanes (eight hits) and the reads of one hit by all lanes both fall on distinct banks:
-// coil-pair chunk q of hit h sits at q ^ (h mod NQ), weight chunk q at q ^ ((h / 2) mod 4).
+// Staging rows hold a hit's 16-byte chunks in order.  Lane h copies the chunks of hit h in an order
+// rotated by h (coil-pair chunk (q + h) mod NQ, weight chunk (q + h / 2) mod 4 at step q), so that
+// the asynchronous copies of the eight lanes of a wavefront fall on distinct banks; the reads of
+// one hit by all lanes are broadcasts or distinct chunks of one row.
 template <int J, int NSL>
 __global__ void __launch_bounds__(kStripWarps * 32, 4) k_spread_strips(StripArgs a) {
     pdl_wait();
@@ -332,13 +333,18 @@ __global__ void __launch_bounds__(kStripWarps * 32, 4) k_spread_strips(StripArgs
             const int nh = min(kStripBatch, item.z - b);
             if (b != item.y && lane < nh) hit = a.t.hits[b + lane];   // later batches of a split part
             if (lane < nh) {
-                const int sw = (lane >> 1) & 3;
                 const float* pw = a.pts.w + (int64_t)hit.x * 16;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) cp_async16(&s_w[warp][lane][4 * (q ^ sw)], pw + 4 * q);
+                for (int q = 0; q < 4; ++q) {
+                    const int qq = (q + (lane >> 1)) & 3;
+                    cp_async16(&s_w[warp][lane][4 * qq], pw + 4 * qq);
+                }
                 const float4* py = yg + (int64_t)hit.x * NQ;
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) cp_async16(&s_y[warp][lane][q ^ (lane & (NQ - 1))], py + q);
+                for (int q = 0; q < NQ; ++q) {
+                    const int qq = (q + lane) & (NQ - 1);
+                    cp_async16(&s_y[warp][lane][qq], py + qq);
+                }
                 s_m[warp][lane] = make_int2((hit.y & 255) - 8, (hit.y >> 8) - 32);
             }
             cp_async_wait_all();
@@ -348,11 +354,11 @@ __global__ void __launch_bounds__(kStripWarps * 32, 4) k_spread_strips(StripArgs
                 const int2 m = s_m[warp][h];
                 const int ta = m.y + s;   // this lane's row tap
                 const float* w = s_w[warp][h];
-                const int sw = (h >> 1) & 3;
-                const float wo = (unsigned)ta < (unsigned)J ? w[4 * ((ta >> 2) ^ sw) + (ta & 3)] : 0.f;
-                const float4 yv = s_y[warp][h][pc ^ (h & (NQ - 1))];
-                const float4 wa = *(const float4*)(w + 4 * (2 ^ sw));
-                const float4 wb = *(const float4*)(w + 4 * (3 ^ sw));
+                const float wr = w[ta & 7];   // row taps 0..7 (zero past J)
+                const float wo = (unsigned)ta < (unsigned)J ? wr : 0.f;
+                const float4 yv = s_y[warp][h][pc];
+                const float4 wa = *(const float4*)(w + 8);
+                const float4 wb = *(const float4*)(w + 12);
                 const float wx[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
                 const float yw[4] = {wo * yv.x, wo * yv.y, wo * yv.z, wo * yv.w};
                 strip_add_J<J>(acc, m.x, wx, yw);
