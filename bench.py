@@ -586,6 +586,13 @@ def cgsense_record(steps, warmup):
         torch.cuda.synchronize()
     n1 = nufft_launch_count()
     ms = [a.elapsed_time(b) for a, b in evs]
+    # one more step, untimed, with the library's per-kernel events: where the 3-D step spends its time
+    op.plan.profile_enable(True)
+    op.plan.profile_read()
+    step()
+    torch.cuda.synchronize()
+    prof = op.plan.profile_read()
+    op.plan.profile_enable(False)
     units = cgsense_units(M, C, D, CG_ITERS)
     rec = {"workload": "cgsense3d: 128x128x96 image, 8 coils, 2,000,000 points (8000 3-D radial spokes x 250, "
                        "random-walk perturbed); loss = ||x_K - x||^2, x_K = %d unrolled CG-SENSE iterations on "
@@ -595,7 +602,8 @@ def cgsense_record(steps, warmup):
            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)), "steps": steps,
            "units_per_step": units, "peak_device_bytes": int(torch.cuda.max_memory_allocated()),
            "plan_workspace_bytes": int(op.plan.info().workspace_bytes), "gpu_launches": n1 - n0,
-           "l2": "inputs larger than L2"}
+           "l2": "inputs larger than L2",
+           "kernels_one_step": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()}}
     return rec, clk.summary()
 
 
@@ -624,7 +632,7 @@ def batched_record(steps, warmup):
     from paper_2111_02912_gb300 import nufft_launch_count
     from paper_2111_02912_gb300.batch import BatchedJacobian
     from paper_2111_02912_gb300.workloads import batched_problems
-    probs = batched_problems(args.serve_problems)
+    probs = batched_problems(64)
     bj = BatchedJacobian(probs, device="cuda", streams=4, autotune=True)
     units = bj.units()
     stream = torch.cuda.current_stream()
