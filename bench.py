@@ -618,7 +618,7 @@ def run_cgsense3d(args):
             "dtype": "c64 (fp32 complex)",
             "data": "synthetic (seeded 3-D radial with random walk, ellipsoid phantom, Gaussian-bump maps)",
             "config": {k: rec[k] for k in ("workload", "units_per_step", "l2", "peak_device_bytes",
-                                           "plan_workspace_bytes")},
+                                           "plan_workspace_bytes", "kernels_one_step")},
             "gpu_launches": rec["gpu_launches"], "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))

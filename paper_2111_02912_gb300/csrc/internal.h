@@ -12,50 +12,76 @@ namespace nj {
 // start; each bin is a contiguous range.
 constexpr int kNbrStride = 64;        // entries per tile in tile_nbr: n, then 27 (start, prefix) pairs, total
 
-// ------------------------------------------------------ 2-D strip geometry
-// The 2-D adjoint spread runs on strip units: NSL consecutive grid rows by kStripW
-// consecutive columns (all coils of a coil group).  Unit u covers rows
-// R = (u / nb1) NSL .. R + NSL - 1 and columns (u % nb1) kStripW .. + kStripW - 1.
+// ---------------------------------------------------------- strip geometry
+// The adjoint spread of the strip kernel runs on strip units: NSL grid "rows" by kStripW
+// consecutive cells of the last axis (the columns), all coils of a coil group.  In 2-D a row is a
+// k0 index and a unit holds NSL consecutive rows; in 3-D a row is a (k0, k1) pair and a unit
+// holds R0 x R1 of them (R0 R1 = NSL), R0 consecutive k0 by R1 consecutive k1.  Unit
+// u = (g0 ng1 + g1) nbl + t covers rows g0 R0 .., g1 R1 .. (g1 = 0, R1 = 1 in 2-D) and columns
+// t kStripW .. + kStripW - 1.
 constexpr int kStripW = 16;           // columns of a strip unit (the accumulators of one lane)
+// 3-D: rows of a unit along dim 1 for NSL rows in all (R0 = NSL / R1 along dim 0), near square
+__host__ __device__ constexpr int strip_rows1(int nsl) { return nsl >= 32 ? 8 : (nsl >= 8 ? 4 : 2); }
 struct StripGeom {
-    int K0, K1, nb1, J, NSL, ngroups;
+    int D;
+    int K0, K1, KL;     // grid edges: dims 0 and 1, and the last (column) axis (KL = K1 in 2-D)
+    int R0, R1;         // rows of a unit along dim 0 and (3-D) dim 1; R1 = 1 in 2-D
+    int ng1, nbl;       // row groups along dim 1 (1 in 2-D), column tiles
+    int J, NSL;
 };
 
-// Strip units reached by the window starting at (k0, k1): the row groups (of NSL rows) holding
-// its J rows (mod K0) times the column tiles (of kStripW columns) holding its J columns (mod K1),
-// at most 5 x 3.  Calls unit(u, sd, dr) once per unit, with the window's start column relative to
-// the unit, sd in [-(J-1), kStripW), and its start-row offset R - k0 in [-(NSL-1), J-1].
+// Distinct groups of R cells (mod K) holding the J cells k .. k + J - 1 of one axis, at most 5:
+// calls f(group, offset) with offset = group start - k (+ K past the wrap), in [-(R-1), J-1].
 template <typename F>
-__device__ __forceinline__ void strip_point_units(const StripGeom& g, int k0, int k1, F unit) {
+__device__ __forceinline__ void strip_axis_groups(int k, int K, int R, int J, F f) {
+    int prev = -1;
+    for (int j = 0; j < J; ++j) {
+        int c = k + j;
+        if (c >= K) c -= K;
+        const int grp = c / R;
+        if (grp == prev) continue;
+        prev = grp;
+        f(grp, grp * R - k + (c < k ? K : 0));
+    }
+}
+
+// Strip units reached by the window starting at cell ix (k0, k1 and, in 3-D, k2): the row groups
+// holding its J rows of every row axis (mod K) times the column tiles holding its J columns (mod
+// KL), at most 3 tiles.  Calls unit(u, sd, dr0, dr1) once per unit, with the window's start
+// column relative to the unit, sd in [-(J-1), kStripW), and its start-row offsets (group start -
+// k) along dim 0 and (3-D) dim 1, in [-(R-1), J-1] (dr1 = 0 in 2-D).
+template <typename F>
+__device__ __forceinline__ void strip_point_units(const StripGeom& g, int4 ix, F unit) {
+    const int kl = g.D == 3 ? ix.z : ix.y;
     int tiles[3], sds[3], nt = 0;
     for (int j = 0; j < g.J; ++j) {
-        int col = k1 + j;
-        if (col >= g.K1) col -= g.K1;
+        int col = kl + j;
+        if (col >= g.KL) col -= g.KL;
         const int t = col / kStripW;
         if (nt == 0 || t != tiles[nt - 1]) {
             if (nt < 3) {
                 tiles[nt] = t;
-                sds[nt] = k1 - t * kStripW - (col < k1 ? g.K1 : 0);   // past the wrap: start lies left
+                sds[nt] = kl - t * kStripW - (col < kl ? g.KL : 0);   // past the wrap: start lies left
             }
             ++nt;
         }
     }
-    int prev = -1;
-    for (int j = 0; j < g.J; ++j) {
-        int row = k0 + j;
-        if (row >= g.K0) row -= g.K0;
-        const int grp = row / g.NSL;
-        if (grp == prev) continue;
-        prev = grp;
-        const int dr = grp * g.NSL - k0 + (row < k0 ? g.K0 : 0);
-        for (int q = 0; q < nt && q < 3; ++q) unit(grp * g.nb1 + tiles[q], sds[q], dr);
-    }
+    if (nt > 3) nt = 3;
+    strip_axis_groups(ix.x, g.K0, g.R0, g.J, [&](int g0, int dr0) {
+        if (g.D == 3) {
+            strip_axis_groups(ix.y, g.K1, g.R1, g.J, [&](int g1, int dr1) {
+                for (int q = 0; q < nt; ++q) unit((g0 * g.ng1 + g1) * g.nbl + tiles[q], sds[q], dr0, dr1);
+            });
+        } else {
+            for (int q = 0; q < nt; ++q) unit(g0 * g.nbl + tiles[q], sds[q], dr0, 0);
+        }
+    });
 }
 
 // Sort-time tables of the strip spread (once per omega, read by every adjoint of those points).
 // A hit is a point whose window reaches a unit: {sorted point index, packed window start}, the
-// start column relative to the unit in bits 0..7 (biased by 8) and the start-row offset R - k0 in
-// bits 8..15 (biased by 32).  The hits of unit u are hits[hoff[u] .. hoff[u + 1]).  Work items are
+// start column relative to the unit in bits 0..7 (biased by 8) and the start-row offsets along
+// dim 0 in bits 8..15 and (3-D) dim 1 in bits 16..23 (biased by 32).  The hits of unit u are hits[hoff[u] .. hoff[u + 1]).  Work items are
 // {unit, first hit, end hit, split index} (split index -1: the unit is one item; else
 // splits[split index] = {part, parts, first partial slot, 0}); the parts of split units come first.
 struct StripTables {

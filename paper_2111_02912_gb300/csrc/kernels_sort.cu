@@ -274,7 +274,7 @@ __global__ void k_bin_scatter(SortArgs a) {
         for (int j = a.J; j < a.wd; ++j) w[d * a.wd + j] = 0.f;
     }
     // 2-D strips: count the point as a hit of every unit its window reaches
-    if (a.strip) strip_point_units(a.sg, ix.x, ix.y, [&](int u, int, int) { atomicAdd(a.st.hcount + u, 1); });
+    if (a.strip) strip_point_units(a.sg, ix, [&](int u, int, int, int) { atomicAdd(a.st.hcount + u, 1); });
 }
 
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s) {

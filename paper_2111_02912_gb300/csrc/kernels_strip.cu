@@ -1,9 +1,10 @@
-// 2-D adjoint interpolation (spread), Sec. II-D: G[k] = sum_i psi(t_i - k) y_i,
-// the transpose of the gather, onto the oversampled grid [K0][K1][C], on strip units.
+// Adjoint interpolation (spread), Sec. II-D: G[k] = sum_i psi(t_i - k) y_i, the transpose of
+// the gather, onto the oversampled grid [K0][K1]([K2])[C], on strip units (2-D and 3-D).
 //
-// A strip unit is NSL grid rows x kStripW columns.  A warp owns one unit (or one
-// part of a unit) for a coil group of CPW = 64 / NSL coils: lane (s, p) holds row
-// R + s, coils 2p and 2p + 1 of the group, all kStripW columns, in registers.
+// A strip unit is NSL grid rows x kStripW columns of the last axis (a row is a k0 index in 2-D,
+// a (k0, k1) pair of an R0 x R1 block in 3-D).  A warp owns one unit (or one part of a unit) for a
+// coil group of CPW = 64 / NSL coils: lane (s, p) holds row s of the unit, coils 2p and 2p + 1 of
+// the group, all kStripW columns, in registers.
 //
 // Sort time (once per omega, read by every adjoint of the same points).  The
 // scatter counts every point as a hit of each unit its window reaches
@@ -20,7 +21,8 @@
 // with asynchronous copies (cp.async), and then every hit is added to the accumulators
 // of all lanes at once: the lane's row tap comes from its row slot, and the column
 // taps land on compile-time register indices through a warp-uniform jump table on
-// the window's start column (strip_cases.inc, generated by gen_strip_cases.py).
+// the window's start column (strip_cases.inc, generated by gen_strip_cases.py); in 3-D the row
+// weight is the product of the lane's taps along dims 0 and 1.
 // There is no shared-memory read-modify-write and no block barrier.
 //
 // Each grid cell belongs to exactly one unit, whose owner writes it (zeros
@@ -100,8 +102,11 @@ __device__ __forceinline__ void block_scan_tiles(int n, int (&carry)[V], Get get
 }
 
 // --------------------------------------------------------------- sort tables
-// Packed window start of a hit: column sd in [-(J-1), 15] and start-row offset dr in [-(NSL-1), J-1].
-__device__ __forceinline__ int strip_meta(int sd, int dr) { return (sd + 8) | ((dr + 32) << 8); }
+// Packed window start of a hit: column sd in [-(J-1), 15] and start-row offsets dr0, dr1 in
+// [-(R-1), J-1] (dr1 = 0 in 2-D).
+__device__ __forceinline__ int strip_meta(int sd, int dr0, int dr1) {
+    return (sd + 8) | ((dr0 + 32) << 8) | ((dr1 + 32) << 16);
+}
 
 // The plan in two launches of 256-thread blocks (unit b * 256 + t in block b, thread t).  Split
 // parts are counted for P * 2^L, L = 0..7: the smallest level whose split parts fit the partial
@@ -225,9 +230,9 @@ __global__ void k_strip_fill(SortArgs a) {
     if (p >= a.m) return;
     const int4 ix = a.pidx[p];
     const StripTables& T = a.st;
-    strip_point_units(a.sg, ix.x, ix.y, [&](int u, int sd, int dr) {
+    strip_point_units(a.sg, ix, [&](int u, int sd, int dr0, int dr1) {
         const int64_t pos = (int64_t)T.hoff[u] + atomicAdd(T.hcur + u, 1);
-        if (pos < T.hit_cap) T.fill_to[pos] = make_int2((int)p, strip_meta(sd, dr));
+        if (pos < T.hit_cap) T.fill_to[pos] = make_int2((int)p, strip_meta(sd, dr0, dr1));
     });
 }
 
@@ -283,18 +288,22 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // rotated by h (coil-pair chunk (q + h) mod NQ, weight chunk (q + h / 2) mod 4 at step q), so that
 // the asynchronous copies of the eight lanes of a wavefront fall on distinct banks; the reads of
 // one hit by all lanes are broadcasts or distinct chunks of one row.
-template <int J, int NSL>
+template <int D, int J, int NSL>
 __global__ void __launch_bounds__(kStripWarps * 32, 4) k_spread_strips(StripArgs a) {
     pdl_wait();
     constexpr int CPW = 64 / NSL;     // coils per warp (a coil pair per lane)
     constexpr int NQ = CPW / 2;       // coil pairs = 16-byte chunks per staged hit
+    constexpr int R1 = D == 3 ? strip_rows1(NSL) : 1, R0 = NSL / R1;   // rows of a unit per row axis
+    constexpr int WS = 8 * D;         // staged weights per hit: 8 per axis, the column taps last
+    constexpr int WQ = WS / 4;        // ... in 16-byte chunks
     __shared__ __align__(16) float4 s_y[kStripWarps][kStripBatch][NQ];
-    __shared__ __align__(16) float s_w[kStripWarps][kStripBatch][16];   // row taps chunks 0-1, column taps 2-3
-    __shared__ int2 s_m[kStripWarps][kStripBatch];                      // {start column, start-row offset}
+    __shared__ __align__(16) float s_w[kStripWarps][kStripBatch][WS];
+    __shared__ int4 s_m[kStripWarps][kStripBatch];                      // {start column, row offsets dr0, dr1}
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cg = blockIdx.y;
     const StripGeom g = a.g;
     const int s = lane / NQ, pc = lane - s * NQ;      // row slot, coil pair
+    const int s0 = s / R1, s1 = s - s0 * R1;          // the slot's row along dims 0 and 1
     const int coil = cg * CPW + 2 * pc;
     const int C = a.C;
     const float4* yg = (const float4*)(a.y + (int64_t)cg * a.pts.m * CPW);   // [M][NQ] pairs of this group
@@ -321,10 +330,11 @@ __global__ void __launch_bounds__(kStripWarps * 32, 4) k_spread_strips(StripArgs
         int4 itemn = make_int4(0, 0, 0, -1);
         if (itn < nitems) itemn = a.t.items[itn];
         const int u = item.x;
-        const int grp = u / g.nb1, tc = u - grp * g.nb1;
-        const int R = grp * NSL, org1 = tc * kStripW;
-        const int NR = min(NSL, g.K0 - R);
-        const int Bt1 = min(kStripW, g.K1 - org1);
+        const int r = u / g.nbl, tc = u - r * g.nbl;
+        const int g0 = D == 3 ? r / g.ng1 : r, g1 = D == 3 ? r - g0 * g.ng1 : 0;
+        const int row0 = g0 * R0 + s0, row1 = g1 * R1 + s1;   // this lane's row (row1: 3-D only)
+        const int org1 = tc * kStripW;
+        const int Bt1 = min(kStripW, g.KL - org1);
 
         float acc[4 * kStripW];   // column k: acc[4k .. 4k+3] = re, im of coil 2 pc, then of coil 2 pc + 1
 #pragma unroll
@@ -333,10 +343,10 @@ __global__ void __launch_bounds__(kStripWarps * 32, 4) k_spread_strips(StripArgs
             const int nh = min(kStripBatch, item.z - b);
             if (b != item.y && lane < nh) hit = a.t.hits[b + lane];   // later batches of a split part
             if (lane < nh) {
-                const float* pw = a.pts.w + (int64_t)hit.x * 16;
+                const float* pw = a.pts.w + (int64_t)hit.x * WS;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int qq = (q + (lane >> 1)) & 3;
+                for (int q = 0; q < WQ; ++q) {   // rotated: 8 lanes of 64- or 96-byte rows on distinct banks
+                    const int qq = D == 2 ? (q + (lane >> 1)) & 3 : (q + (lane >> 2)) % WQ;
                     cp_async16(&s_w[warp][lane][4 * qq], pw + 4 * qq);
                 }
                 const float4* py = yg + (int64_t)hit.x * NQ;
@@ -345,20 +355,23 @@ __global__ void __launch_bounds__(kStripWarps * 32, 4) k_spread_strips(StripArgs
                     const int qq = (q + lane) & (NQ - 1);
                     cp_async16(&s_y[warp][lane][qq], py + qq);
                 }
-                s_m[warp][lane] = make_int2((hit.y & 255) - 8, (hit.y >> 8) - 32);
+                s_m[warp][lane] = make_int4((hit.y & 255) - 8, ((hit.y >> 8) & 255) - 32, ((hit.y >> 16) & 255) - 32, 0);
             }
             cp_async_wait_all();
             __syncwarp();
 #pragma unroll 2
             for (int h = 0; h < nh; ++h) {
-                const int2 m = s_m[warp][h];
-                const int ta = m.y + s;   // this lane's row tap
+                const int4 m = s_m[warp][h];
                 const float* w = s_w[warp][h];
-                const float wr = w[ta & 7];   // row taps 0..7 (zero past J)
-                const float wo = (unsigned)ta < (unsigned)J ? wr : 0.f;
+                const int ta = m.y + s0;   // this lane's row tap along dim 0 (taps 0..7, zero past J)
+                float wo = (unsigned)ta < (unsigned)J ? w[ta & 7] : 0.f;
+                if (D == 3) {              // times its row tap along dim 1
+                    const int tb = m.z + s1;
+                    wo = (unsigned)tb < (unsigned)J ? wo * w[8 + (tb & 7)] : 0.f;
+                }
                 const float4 yv = s_y[warp][h][pc];
-                const float4 wa = *(const float4*)(w + 8);
-                const float4 wb = *(const float4*)(w + 12);
+                const float4 wa = *(const float4*)(w + 8 * (D - 1));
+                const float4 wb = *(const float4*)(w + 8 * (D - 1) + 4);
                 const float wx[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
                 const float yw[4] = {wo * yv.x, wo * yv.y, wo * yv.z, wo * yv.w};
                 strip_add_J<J>(acc, m.x, wx, yw);
@@ -369,7 +382,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, 4) k_spread_strips(StripArgs
         int2 hitn = make_int2(0, 0);
         if (itn < nitems && lane < itemn.z - itemn.y) hitn = a.t.hits[itemn.y + lane];
 
-        const bool rok = s < NR;
+        const bool rok = row0 < g.K0 && (D == 2 || row1 < g.K1);
         bool write = item.w < 0;
         if (!write) {   // split unit: deposit this part, count it; the last part adds all parts in order
             const int4 sp = a.t.splits[item.w];
@@ -403,7 +416,8 @@ __global__ void __launch_bounds__(kStripWarps * 32, 4) k_spread_strips(StripArgs
             }
         }
         if (write && rok && coil < C) {
-            float2* dst = a.grid + ((int64_t)(R + s) * g.K1 + org1) * C + coil;
+            const int64_t cell = D == 3 ? ((int64_t)row0 * g.K1 + row1) * g.KL + org1 : (int64_t)row0 * g.KL + org1;
+            float2* dst = a.grid + cell * C + coil;
             if (coil + 1 < C && (C & 1) == 0) {   // both coils, one 16-byte store per column
 #pragma unroll
                 for (int q = 0; q < kStripW; ++q)
@@ -445,34 +459,39 @@ static int resident_blocks(int threads) {
     return v;
 }
 
-template <int J, int NSL>
+template <int D, int J, int NSL>
 static void strips_launch(const StripArgs& a, cudaStream_t s) {
     constexpr int threads = kStripWarps * 32;
     const int need = (a.max_items + kStripWarps - 1) / kStripWarps;
-    const int blocks = std::max(1, std::min(need, resident_blocks<k_spread_strips<J, NSL>>(threads)));
-    (void)launch_pdl(k_spread_strips<J, NSL>, dim3((unsigned)blocks, (unsigned)a.ncg), threads, 0, s, a);
+    const int blocks = std::max(1, std::min(need, resident_blocks<k_spread_strips<D, J, NSL>>(threads)));
+    (void)launch_pdl(k_spread_strips<D, J, NSL>, dim3((unsigned)blocks, (unsigned)a.ncg), threads, 0, s, a);
 }
 
-template <int J>
+template <int D, int J>
 static cudaError_t strips_j(const StripArgs& a, cudaStream_t s) {
     switch (a.g.NSL) {
-        case 4: strips_launch<J, 4>(a, s); break;
-        case 8: strips_launch<J, 8>(a, s); break;
-        case 16: strips_launch<J, 16>(a, s); break;
-        default: strips_launch<J, 32>(a, s); break;
+        case 4: strips_launch<D, J, 4>(a, s); break;
+        case 8: strips_launch<D, J, 8>(a, s); break;
+        case 16: strips_launch<D, J, 16>(a, s); break;
+        default: strips_launch<D, J, 32>(a, s); break;
     }
     return cudaGetLastError();
 }
 
+template <int D>
+static cudaError_t strips_d(const StripArgs& a, cudaStream_t s) {
+    switch (a.g.J) {
+        case 4: return strips_j<D, 4>(a, s);
+        case 5: return strips_j<D, 5>(a, s);
+        case 6: return strips_j<D, 6>(a, s);
+        case 7: return strips_j<D, 7>(a, s);
+        default: return strips_j<D, 8>(a, s);
+    }
+}
+
 cudaError_t launch_spread_strips(const StripArgs& a, cudaStream_t s) {
     if (a.max_items == 0) return cudaSuccess;
-    switch (a.g.J) {
-        case 4: return strips_j<4>(a, s);
-        case 5: return strips_j<5>(a, s);
-        case 6: return strips_j<6>(a, s);
-        case 7: return strips_j<7>(a, s);
-        default: return strips_j<8>(a, s);
-    }
+    return a.g.D == 3 ? strips_d<3>(a, s) : strips_d<2>(a, s);
 }
 
 // Coil values in sorted point order, in the strip layout [C / cpt][M][cpt].

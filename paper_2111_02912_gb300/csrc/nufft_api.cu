@@ -91,7 +91,7 @@ struct nufft_plan_s {
     int kernel_mode = NUFFT_KERNEL_DIRECT, tab_L = 0, tab_n = 0;   // table mode: L samples per unit
     float* d_kbtab = nullptr;      // [tab_n + 2] psi(l / tab_L), zero from tab_n on
     int2* d_hits_tmp = nullptr;    // [hit_cap] the fill's list before ordering (deterministic only)
-    int NSL = 2, nunits = 0, strip_P = 64, strip_slots = 0, ncg_max = 1;
+    int NSL = 2, SR0 = 2, SR1 = 1, nunits = 0, strip_P = 64, strip_slots = 0, ncg_max = 1;
     float2* d_ys = nullptr;        // [ncg_max][M_cap][64 / NSL] coil values in sorted point order
     float2* d_partial = nullptr;   // [strip_slots][ncg_max][kStripW][32] coil pairs (float4)
     int* d_counters = nullptr;     // [strip_slots][ncg_max], zero between calls
@@ -293,20 +293,25 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
     p.cell_spread = p.D >= 2 && tcells <= 512;
     for (int d = 0; d < p.D; ++d) p.cell_spread = p.cell_spread && p.B[d] + p.J - 1 <= p.K[d];
     p.P = p.cell_spread ? (int)tcells : (p.D == 3 ? 1024 : 512);
-    // 2-D strips: lanes are NSL row slots x 32 / NSL coil pairs, chosen from max_coils; a window
-    // must not reach a unit twice along either axis
+    // strips (2-D and 3-D): lanes are NSL row slots x 32 / NSL coil pairs, chosen from max_coils;
+    // a window must not reach a unit twice along any axis
     {
         // coils per warp (a coil pair per lane): 16, 8, 4 or 2; NSL = 64 / coils per warp
         const int cpw = p.maxC >= 9 ? 16 : (p.maxC >= 5 ? 8 : (p.maxC >= 3 ? 4 : 2));
         p.NSL = 64 / cpw;
         p.ncg_max = (p.maxC + cpw - 1) / cpw;
-        // a window must not reach a unit twice: K1 >= 16 + J - 1 columns, K0 >= NSL + J - 1 rows
-        p.strip = p.D == 2 && p.K[1] >= kStripW + p.J - 1 && p.K[0] >= p.NSL + p.J - 1;
+        p.SR1 = p.D == 3 ? strip_rows1(p.NSL) : 1;
+        p.SR0 = p.NSL / p.SR1;
+        // a window must not reach a unit twice: 16 + J - 1 columns along the last axis, R + J - 1
+        // rows along each row axis (R = NSL in 2-D, R0 and R1 in 3-D)
+        const int64_t KL = p.K[p.D - 1];
+        p.strip = p.D >= 2 && KL >= kStripW + p.J - 1 && p.K[0] >= p.SR0 + p.J - 1 &&
+                  (p.D == 2 || p.K[1] >= p.SR1 + p.J - 1);
         if (o->spread_variant == NUFFT_SPREAD_TILES || o->spread_variant == NUFFT_SPREAD_GENERAL) p.strip = false;
         if (o->spread_variant == NUFFT_SPREAD_GENERAL) p.cell_spread = false;
         if (o->spread_variant == NUFFT_SPREAD_STRIPS && !p.strip)
-            return fail(NUFFT_ERR_UNSUPPORTED, "strip spread needs D = 2, 16-cell column bins and a grid of at least "
-                                               "16 + J - 1 columns and 32 / coils + J - 1 rows");
+            return fail(NUFFT_ERR_UNSUPPORTED, "strip spread needs D >= 2 and a grid of at least 16 + J - 1 cells "
+                                               "along the last axis and R + J - 1 along the others (R: unit rows)");
         if (o->spread_variant == NUFFT_SPREAD_TILES && !p.cell_spread)
             return fail(NUFFT_ERR_UNSUPPORTED, "tile spread needs D >= 2, at most 512 cells per bin and bins of at "
                                                "most K - J + 1 cells");
@@ -319,9 +324,12 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
         }
         p.deterministic = o->deterministic != 0;
         if (p.deterministic && !p.strip)
-            return fail(NUFFT_ERR_UNSUPPORTED, "deterministic results need the 2-D strip spread");
+            return fail(NUFFT_ERR_UNSUPPORTED, "deterministic results need the strip spread");
         if (p.strip) {
-            p.nunits = (int)(((p.K[0] + p.NSL - 1) / p.NSL) * ((p.K[1] + kStripW - 1) / kStripW));
+            int64_t nu = ((p.K[0] + p.SR0 - 1) / p.SR0) * ((KL + kStripW - 1) / kStripW);
+            if (p.D == 3) nu *= (p.K[1] + p.SR1 - 1) / p.SR1;
+            if (nu >= ((int64_t)1 << 30)) return fail(NUFFT_ERR_UNSUPPORTED, "too many strip units");
+            p.nunits = (int)nu;
             // partial-sum slots for split units (8 KB each): ~nunits / 4, at most 16 MB (the plan
             // lengthens the parts of split units when they would need more)
             p.strip_slots = std::max(64, std::min(2048 / p.ncg_max, p.nunits / 4));
@@ -346,7 +354,7 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
         p.tab_n = p.tab_L * p.J / 2;
     }
     p.wd = p.strip ? 8 : p.J;   // the strip spread reads the column weights as two 16-byte loads
-    p.ws = p.strip ? 16 : (p.D * p.J + 3) & ~3;
+    p.ws = p.strip ? 8 * p.D : (p.D * p.J + 3) & ~3;
     for (int d = 0; d < p.D; ++d) {
         const double c = (double)p.K[d] / (2.0 * M_PI);
         p.c_hi[d] = (float)c;
@@ -404,7 +412,10 @@ size_t strip_bytes(const nufft_plan_s& p) {
 // Strip units a point's window can reach: its J rows span at most ceil((J - 1) / NSL) + 1 row
 // groups, one more where they wrap past the shorter last group, and its J columns at most three
 // column tiles (two, and a narrow last one).
-int64_t strip_hits_per_point(const nufft_plan_s& p) { return 3 * ((p.J - 2) / p.NSL + 3); }
+int64_t strip_hits_per_point(const nufft_plan_s& p) {
+    const int64_t rows0 = (p.J - 2) / p.SR0 + 3;
+    return p.D == 3 ? 3 * rows0 * ((p.J - 2) / p.SR1 + 3) : 3 * rows0;
+}
 
 size_t point_bytes(const nufft_plan_s& p, int64_t cap) {
     size_t b = (size_t)cap * (2 * sizeof(int) + sizeof(int4) + sizeof(float4) + (p.ws + p.D) * sizeof(float)) +
@@ -468,12 +479,16 @@ StripTables strip_tables(const nufft_plan_s& p) {
 
 StripGeom strip_geom(const nufft_plan_s& p) {
     StripGeom g{};
+    g.D = p.D;
     g.K0 = (int)p.K[0];
-    g.K1 = (int)p.K[1];
-    g.nb1 = (int)((p.K[1] + kStripW - 1) / kStripW);
+    g.K1 = p.D >= 2 ? (int)p.K[1] : 1;
+    g.KL = (int)p.K[p.D - 1];
+    g.R0 = p.SR0;
+    g.R1 = p.SR1;
+    g.ng1 = p.D == 3 ? (int)((p.K[1] + p.SR1 - 1) / p.SR1) : 1;
+    g.nbl = (int)((g.KL + kStripW - 1) / kStripW);
     g.J = p.J;
     g.NSL = p.NSL;
-    g.ngroups = (int)((p.K[0] + p.NSL - 1) / p.NSL);
     return g;
 }
 

@@ -100,7 +100,7 @@ def test_all_products_match_same_kernel_oracle(name, shape, M, C, maps, opts):
     assert max_rel(host(gx), gx_ref) < TOL_SAME
 
 
-# The 2-D strip spread: every coils-per-warp width (64 / NSL coils for NSL rows), J 4..8, grids
+# The strip spread: every coils-per-warp width (64 / NSL coils for NSL rows), J 4..8, grids
 # just wide enough for it (K1 = 16 + J - 1 columns, K0 = NSL + J - 1 rows: windows wrap around both
 # axes), several coil groups, and the two other spread kernels on the same problem.
 STRIP_CASES = [
@@ -121,6 +121,19 @@ STRIP_CASES = [
     ("strip_variant_tiles", (32, 40), 1500, 3, True, dict(spread="tiles")),
     ("strip_variant_general", (32, 40), 1500, 3, True, dict(spread="general")),
     ("strip_variant_strips", (32, 40), 1500, 3, True, dict(spread="strips")),
+    # 3-D strips: units of R0 x R1 rows (k0, k1) by 16 cells of the last axis, every coils-per-warp
+    # width (R0 x R1 = 4 x 8, 2 x 4, 4 x 4, 2 x 2), grids just wide enough, ragged row groups and
+    # column tiles, two coil groups, and the cell-owner kernel on the same kind of problem
+    ("strip3d_c2", (16, 20, 24), 3000, 2, True, {}),
+    ("strip3d_c5", (12, 16, 20), 2000, 5, True, {}),
+    ("strip3d_c8", (16, 12, 16), 2500, 8, True, {}),
+    ("strip3d_c16_J4", (10, 12, 14), 1500, 16, True, dict(J=4)),
+    ("strip3d_narrow_J8", (8, 8, 12), 800, 3, True, dict(J=8)),          # K = 16 x 16 x 24
+    ("strip3d_J5_ragged_tile", (10, 14, 18), 1500, 6, True, dict(J=5)),  # last column tile 4 wide
+    ("strip3d_J7", (14, 10, 12), 1200, 4, True, dict(J=7)),
+    ("strip3d_sigma125_ragged_rows", (24, 16, 20), 2000, 3, True, dict(sigma=1.25)),   # K = 30 x 20 x 30
+    ("strip3d_two_coil_groups", (12, 12, 16), 1000, 20, True, {}),
+    ("strip3d_variant_tiles", (16, 20, 24), 2000, 3, True, dict(spread="tiles")),
 ]
 
 
@@ -323,6 +336,8 @@ def test_radial3d_full_size_sampled_against_exact_nudft():
     ("det_radial_like", (48, 40), 3000, 16, False),
     ("det_clustered_split_units", (32, 32), 20000, 4, True),   # units split into parts: ordered combine
     ("det_two_coil_groups", (24, 40), 1500, 20, False),
+    ("det_3d", (16, 20, 24), 3000, 8, False),
+    ("det_3d_clustered_split_units", (12, 12, 16), 12000, 2, True),
 ])
 def test_deterministic_adjoint_is_bitwise_reproducible(name, shape, M, C, clustered):
     """deterministic=1: repeated calls, and a re-sort of the same omega, give bitwise equal results."""
