@@ -78,9 +78,10 @@ typedef struct {
                          pi sqrt((J/sigma)^2 (sigma-1/2)^2 - 0.8)) */
     int max_coils;    /* largest C any call on this plan will pass, 1..NUFFT_MAX_COILS (0 -> 1) */
     int bin_size[3];  /* spread tile edge per dim (0 -> automatic: 256, 16x16, 8x8x8) */
-    int deterministic; /* 1: every output is bitwise reproducible from call to call (the 2-D
-                          adjoint adds its terms in an order fixed by the sort); 0: fastest
-                          order (the adjoint then agrees to rounding between calls) */
+    int deterministic; /* 1: every output is bitwise reproducible from call to call (the strip
+                          adjoint adds its terms in an order fixed by the sort; needs the strip
+                          spread); 0: fastest order (the adjoint then agrees to rounding between
+                          calls) */
     int spread_variant; /* adjoint spread kernel: NUFFT_SPREAD_AUTO (0), _STRIPS, _TILES, _GENERAL */
     int strip_part;   /* strip spread: hits one warp adds before a unit is split into parts
                          (a power of two, 8..4096; 0 -> 64) */
@@ -97,9 +98,11 @@ enum { NUFFT_KERNEL_DIRECT = 0, NUFFT_KERNEL_TABLE = 1 };
 
 /* Adjoint spread kernels (nufft_opts.spread_variant), all computing the transpose of the
  * interpolation (Sec. II-D); AUTO takes STRIPS where it applies, else TILES, else GENERAL.
- *   STRIPS  2-D only: a warp owns NSL grid rows x 16 columns in registers (NSL = 64 / coils per
- *           warp: 4 for 16 coils, from max_coils); needs a grid of at least 16 + J - 1 columns
- *           and NSL + J - 1 rows.
+ *   STRIPS  2-D and 3-D: a warp owns NSL grid rows x 16 cells of the last axis in registers
+ *           (NSL = 64 / coils per warp: 4 for 16 coils, from max_coils; in 3-D a row is a (k0, k1)
+ *           pair of an R0 x R1 block, R0 R1 = NSL); needs a grid of at least 16 + J - 1 cells
+ *           along the last axis and R + J - 1 along each other axis (R = NSL in 2-D, R0 and R1
+ *           in 3-D).
  *   TILES   2-D / 3-D: a block owns one bin tile in shared memory (row or cell owners).
  *   GENERAL any D: shared-memory atomics on bin tiles.
  * Asking for a variant that does not apply to the plan returns NUFFT_ERR_UNSUPPORTED. */
