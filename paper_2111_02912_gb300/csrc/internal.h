@@ -295,6 +295,7 @@ struct GatherArgs {
     const float2* grid;   // [K...][ch], ch = nd * C, channel = dblock * C + c
     int C, nd, has_plain;
     int G, lgG;           // lanes per point (power of two <= 32)
+    int W;                // coils per lane slot (1, 2 or 4: single coils, pairs, quads), host dispatch
     KbPoly kb;
     int64_t M;
     float2* y;            // [C][M]
@@ -305,6 +306,8 @@ struct GatherArgs {
     float2* v_sorted;     // VJP: if set, v is also written here in sorted point order, [C][M]
     int v_sorted_cpt;     // ... in the strip layout [C / cpt][M][cpt] instead, when > 0
 };
+// cpl: lane slots per lane (coils l + k G), or 0 for coil pairs, kGatherQuads for coil quads
+constexpr int kGatherQuads = -4;
 cudaError_t launch_gather_d1(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);
 cudaError_t launch_gather_d2(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);
 cudaError_t launch_gather_d3(GatherMode mode, const GatherArgs& a, int cpl, cudaStream_t s);

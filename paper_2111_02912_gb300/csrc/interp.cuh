@@ -26,9 +26,17 @@ __device__ __forceinline__ void group_weights(float* w, const float* pw, int wd,
     }
 }
 
-// PAIR: lane l owns the coil pairs (2 (l + k G), 2 (l + k G) + 1), read as one 16-byte load
-// (C even); otherwise lane l owns coils l + k G.
-template <int D, int J, int ND, int CPL, int MODE, bool PAIR>
+// 32-byte read-only load (four complex coil values), one instruction.
+__device__ __forceinline__ void ldg_v8(const float2* p, float4& lo, float4& hi) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
+        : "l"(p));
+}
+
+// W coils per lane slot: lane l owns coils W (l + k G) .. W (l + k G) + W - 1, read as one load of
+// 8 W bytes (W = 2: a 16-byte load, C even; W = 4: a 32-byte load, C a multiple of 4; W = 1: one
+// coil).
+template <int D, int J, int ND, int CPL, int MODE, int W>
 __device__ __forceinline__ void gather_body(const GatherArgs& a) {
     extern __shared__ float wsm[];   // [groups][D * J]
     const int tid = threadIdx.x;
@@ -50,7 +58,6 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a) {
 
     const int C = a.C;
     const int chs = ND * C;   // channel stride of one grid cell
-    constexpr int W = PAIR ? 2 : 1;   // coils per lane slot
     bool ok[CPL];
     int lofs[CPL];   // coil offset of slot k; slots past the last coil read coil 0 (never stored)
 #pragma unroll
@@ -89,7 +96,18 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a) {
             for (int q = 0; q < ND; ++q)
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {   // unconditional loads: all taps in flight together
-                        if (PAIR) {
+                        if constexpr (W == 4) {
+                            float4 g, h;
+                            ldg_v8(gp + q * C + lofs[k], g, h);
+                            acc[q][k][0].x = fmaf(wt, g.x, acc[q][k][0].x);
+                            acc[q][k][0].y = fmaf(wt, g.y, acc[q][k][0].y);
+                            acc[q][k][1].x = fmaf(wt, g.z, acc[q][k][1].x);
+                            acc[q][k][1].y = fmaf(wt, g.w, acc[q][k][1].y);
+                            acc[q][k][2].x = fmaf(wt, h.x, acc[q][k][2].x);
+                            acc[q][k][2].y = fmaf(wt, h.y, acc[q][k][2].y);
+                            acc[q][k][W - 1].x = fmaf(wt, h.z, acc[q][k][W - 1].x);
+                            acc[q][k][W - 1].y = fmaf(wt, h.w, acc[q][k][W - 1].y);
+                        } else if constexpr (W == 2) {
                             const float4 g = __ldg((const float4*)(gp + q * C + lofs[k]));
                             acc[q][k][0].x = fmaf(wt, g.x, acc[q][k][0].x);
                             acc[q][k][0].y = fmaf(wt, g.y, acc[q][k][0].y);
@@ -199,19 +217,19 @@ __device__ __forceinline__ void gather_body(const GatherArgs& a) {
     }
 }
 
-template <int D, int J, int ND, int CPL, int MODE, bool PAIR>
+template <int D, int J, int ND, int CPL, int MODE, int W>
 __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
     pdl_wait();
-    gather_body<D, J, ND, CPL, MODE, PAIR>(a);
+    gather_body<D, J, ND, CPL, MODE, W>(a);
 }
 
 // The gathers wait on their tap loads.  The 2-D VJP with coil pairs is held to 64 registers (no
 // spill for any J) so that four blocks share an SM: measured 40.3 -> 39.1 us on the 640^2, 16-coil
 // case.  The forward at 40 or 48 registers spills and gains nothing; the other VJP kinds spill at 64.
-template <int D, int J, int ND, int CPL, int MODE, bool PAIR>
+template <int D, int J, int ND, int CPL, int MODE, int W>
 __global__ void __launch_bounds__(256, 4) k_gather_occ4(GatherArgs a) {
     pdl_wait();
-    gather_body<D, J, ND, CPL, MODE, PAIR>(a);
+    gather_body<D, J, ND, CPL, MODE, W>(a);
 }
 
 template <int D, int J, int ND, int MODE>
@@ -221,12 +239,14 @@ static cudaError_t gather_cpl(const GatherArgs& a, int cpl, cudaStream_t s) {
     const unsigned blocks = (unsigned)((a.pts.m + gpb - 1) / gpb);
     const size_t smem = (size_t)gpb * D * J * sizeof(float);
     if (blocks == 0) return cudaSuccess;
-    if (cpl == 0) {   // coil pairs
-        if constexpr (D == 2 && MODE == GM_VJP) (void)launch_pdl(k_gather_occ4<D, J, ND, 1, MODE, true>, blocks, threads, smem, s, a);
-        else (void)launch_pdl(k_gather<D, J, ND, 1, MODE, true>, blocks, threads, smem, s, a);
+    if (cpl == kGatherQuads) {   // coil quads
+        (void)launch_pdl(k_gather<D, J, ND, 1, MODE, 4>, blocks, threads, smem, s, a);
+    } else if (cpl == 0) {   // coil pairs
+        if constexpr (D == 2 && MODE == GM_VJP) (void)launch_pdl(k_gather_occ4<D, J, ND, 1, MODE, 2>, blocks, threads, smem, s, a);
+        else (void)launch_pdl(k_gather<D, J, ND, 1, MODE, 2>, blocks, threads, smem, s, a);
     }
-    else if (cpl == 1) (void)launch_pdl(k_gather<D, J, ND, 1, MODE, false>, blocks, threads, smem, s, a);
-    else (void)launch_pdl(k_gather<D, J, ND, 4, MODE, false>, blocks, threads, smem, s, a);   // C up to 4 G = 128
+    else if (cpl == 1) (void)launch_pdl(k_gather<D, J, ND, 1, MODE, 1>, blocks, threads, smem, s, a);
+    else (void)launch_pdl(k_gather<D, J, ND, 4, MODE, 1>, blocks, threads, smem, s, a);   // C up to 4 G = 128
     return cudaGetLastError();
 }
 
