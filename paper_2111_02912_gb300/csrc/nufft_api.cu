@@ -122,6 +122,10 @@ struct nufft_plan_s {
     // first kernel that reads the sorted points.  Fork and join stay inside one call.
     cudaStream_t aux = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr, join2_ev = nullptr;
+    // A VJP with both outputs on 2-D strips runs its adjoint (grad_x) on aux2 beside the
+    // omega-gradient gather, forked and joined inside the call.
+    cudaStream_t aux2 = nullptr;
+    cudaEvent_t fork2_ev = nullptr, done2_ev = nullptr;
     bool sort_pending = false;   // eager: omega copied by set_points, not yet sorted
     bool join_pending = false;   // sort launched on aux, not yet joined into a stream
     bool join2_pending = false;  // strip plan and fill launched on aux after the join event, not yet joined
@@ -236,6 +240,9 @@ void free_plan(nufft_plan_s* p) {
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     if (p->join_ev) cudaEventDestroy(p->join_ev);
     if (p->join2_ev) cudaEventDestroy(p->join2_ev);
+    if (p->aux2) cudaStreamDestroy(p->aux2);
+    if (p->fork2_ev) cudaEventDestroy(p->fork2_ev);
+    if (p->done2_ev) cudaEventDestroy(p->done2_ev);
     for (auto& e : p->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto e : p->pool) cudaEventDestroy(e);
     delete p;
@@ -786,14 +793,17 @@ int forward_grids(nufft_plan_s* p, int C, int nd, int has_plain, const float2* x
     return NUFFT_OK;
 }
 
-int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cudaStream_t s);
+int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cudaStream_t s,
+                   float2* gbuf = nullptr, float2* tbuf = nullptr);
 
 // Adjoint of the interpolation + FFT + scaling for C coil channels of y.
 // ysorted: y already copied into T in sorted point order (by the VJP gather), else null.
 int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, float2* xout, cudaStream_t s,
-                 const float2* ysorted = nullptr) {
+                 const float2* ysorted = nullptr, float2* gbuf = nullptr, float2* tbuf = nullptr) {
     const int D = p->D;
     int st;
+    if (!gbuf) gbuf = p->d_G;
+    if (!tbuf) tbuf = p->d_T;
     if (p->strip) {
         // 2-D strips: every grid cell written once by its unit; y in sorted point-major order
         StripArgs ta{};
@@ -804,7 +814,7 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
         ta.C = C;
         const int cpt = 64 / p->NSL;   // coils per warp
         ta.ncg = (C + cpt - 1) / cpt;
-        ta.grid = p->d_G;
+        ta.grid = gbuf;
         ta.partial = p->d_partial;
         ta.counters = p->d_counters;
         if (ysorted) {
@@ -817,7 +827,7 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
         }
         if ((st = strip_join(p, s))) return st;
         if ((st = launch(p, PK_SPREAD, s, [&] { return launch_spread_strips(ta, s); }))) return st;
-        return inverse_passes(p, C, smaps, xout, s);
+        return inverse_passes(p, C, smaps, xout, s, gbuf, tbuf);
     }
     // spread: output-driven tiles; only tiles split over several work items are cleared first
     SpreadArgs sa{};
@@ -871,12 +881,16 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
     return inverse_passes(p, C, smaps, xout, s);
 }
 
-// Inverse FFT passes over the spread grid in p->d_G, dim 0 first; the last one crops, scales and
-// applies the conjugate maps (summing the coils) or writes one image per coil.
-int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cudaStream_t s) {
+// Inverse FFT passes over the spread grid in gbuf (p->d_G), dim 0 first, intermediates alternating
+// with tbuf (p->d_T); the last one crops, scales and applies the conjugate maps (summing the coils)
+// or writes one image per coil.
+int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cudaStream_t s, float2* gbuf,
+                   float2* tbuf) {
     const int D = p->D;
     int st;
-    const float2* in = p->d_G;
+    if (!gbuf) gbuf = p->d_G;
+    if (!tbuf) tbuf = p->d_T;
+    const float2* in = gbuf;
     ImageSide im = image_side(p, C, nullptr, smaps, xout, 0);
     for (int d = 0; d < D; ++d) {
         const int L = (int)p->K[d];
@@ -885,7 +899,7 @@ int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cu
         for (int e = d + 1; e < D; ++e) S *= p->K[e];
         const bool last = d == D - 1;
         const bool coil_sum = last && smaps != nullptr;
-        float2* out = last ? nullptr : ((d % 2 == 0) ? p->d_T : p->d_G);
+        float2* out = last ? nullptr : ((d % 2 == 0) ? tbuf : gbuf);
         Tile t = pick_tile(L, B, S, coil_sum, (int)p->N[d]);
         LinePass a{};
         a.ax = p->axis[d];
@@ -906,7 +920,7 @@ int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cu
         a.im = im;
         float2* part = nullptr;
         if (coil_sum && chunks > 1) {   // partial coil sums per chunk, added in order afterwards
-            part = (in == p->d_G) ? p->d_T : p->d_G;
+            part = (in == gbuf) ? tbuf : gbuf;
             a.im.xout = part;
             a.im.xout_stride = p->Nimg;
         }
@@ -1085,7 +1099,10 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
     if (cudaStreamCreateWithPriority(&p->aux, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->join2_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&p->join2_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->aux2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->fork2_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->done2_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         free_plan(p);
         return fail(NUFFT_ERR_CUDA, "stream or event creation failed");
@@ -1151,6 +1168,13 @@ int nufft_jvp_omega(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cf
     return finish_call(p, s, launch(p, PK_GATHER_JVP, s, [&] { return launch_gather(GM_JVP, g, cpl, s); }));
 }
 
+// The two-stream VJP applies to 2-D strip plans with their own streams, with points, and with a
+// last inverse pass that needs no partial coil sums (16 coils or fewer with maps: one block sums
+// them all), whose buffer would be the one the omega chain uses.
+bool dual_vjp(const nufft_plan_s* p, int C, bool maps) {
+    return p->aux2 && p->strip && p->D == 2 && p->M > 0 && (!maps || C <= 16);
+}
+
 int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cfloat* smaps, const nufft_cfloat* v,
                       float* grad_omega, nufft_cfloat* grad_x, void* stream) {
     int st;
@@ -1162,6 +1186,32 @@ int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_
     // last forward pass has read it) for the adjoint's spread, which then needs no reorder pass.
     const float2* vsorted = nullptr;
     if ((st = sort_rest(p, s))) return st;
+    if (grad_omega && grad_x && dual_vjp(p, C, smaps != nullptr)) {
+        // grad_x on aux2 beside the omega-gradient chain on s: the adjoint's grid and intermediate
+        // take the channel block that the D-channel forward grids leave free (the workspace holds
+        // 1 + D channel blocks), so the two chains share no buffer
+        const int64_t N0K1 = p->N[0] * p->K[1];
+        float2* gbuf = p->d_G + (size_t)p->Ktot * C * p->D;
+        float2* tbuf = p->d_T + (size_t)N0K1 * C * p->D;
+        NJ_CUDA(cudaEventRecord(p->fork2_ev, s));
+        NJ_CUDA(cudaStreamWaitEvent(p->aux2, p->fork2_ev, 0));
+        // the sorted points and the strip tables, when they come from a sort of this call
+        if (p->join2_pending) NJ_CUDA(cudaStreamWaitEvent(p->aux2, p->join2_ev, 0));
+        else if (p->join_pending) NJ_CUDA(cudaStreamWaitEvent(p->aux2, p->join_ev, 0));
+        if ((st = adjoint_impl(p, C, (const float2*)v, (const float2*)smaps, (float2*)grad_x, p->aux2, nullptr,
+                               gbuf, tbuf)))
+            return st;
+        NJ_CUDA(cudaEventRecord(p->done2_ev, p->aux2));
+        if ((st = forward_grids(p, C, p->D, 0, (const float2*)x, (const float2*)smaps, s))) return st;
+        if ((st = sort_join(p, s))) return st;
+        GatherArgs g = gather_args(p, C, p->D, 0);
+        g.v = (const float2*)v;
+        g.grad = grad_omega;
+        const int cpl = gather_cpl(g);
+        if ((st = launch(p, PK_GATHER_VJP, s, [&] { return launch_gather(GM_VJP, g, cpl, s); }))) return st;
+        NJ_CUDA(cudaStreamWaitEvent(s, p->done2_ev, 0));
+        return finish_call(p, s, NUFFT_OK);
+    }
     if (grad_omega && p->M > 0) {
         if ((st = forward_grids(p, C, p->D, 0, (const float2*)x, (const float2*)smaps, s))) return st;
         if ((st = sort_join(p, s))) return st;
