@@ -145,7 +145,10 @@ int nufft_jvp_omega(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cf
  *   grad_omega[d][i] = sum_c Re{ conj(v_ci) (-i) [A(s_c . x . r^[d])]_i }   (float [D][M])
  *   grad_x = E' v                                                          (as nufft_adjoint)
  * Either output may be NULL to skip it.  The adjoint operator's omega-VJP
- * (Eq. (e,A'y)) is this call with (x, v) <- (incoming image gradient, y). */
+ * (Eq. (e,A'y)) is this call with (x, v) <- (incoming image gradient, y).
+ * With both outputs on a 2-D strip plan (and at most 16 coils when smaps != NULL),
+ * grad_x is computed on a second stream of the plan beside grad_omega, forked from
+ * and joined back into `stream` inside the call; the call stays stream-ordered. */
 int nufft_vjp_omega_x(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cfloat* smaps,
                       const nufft_cfloat* v, float* grad_omega, nufft_cfloat* grad_x, void* stream);
 
