@@ -47,7 +47,7 @@ __device__ __forceinline__ float kb_table(const float* __restrict__ tab, float L
 // first tap u0 = t - k0_unwrapped in [J/2 - 1, J/2); tap j has offset u0 - j.
 // idx.w holds the caller's point index.  w holds the D*J kernel weights of
 // each sorted point, psi(u0_d - j) at w[i * ws + d * wd + j] (wd = J and ws =
-// D*J rounded up to a multiple of 4; for the 2-D strip spread wd = 8, ws = 16, the
+// D*J rounded up to a multiple of 4; for the strip spread wd = 8, ws = 8 D, the
 // pads zero), evaluated once per omega by the sort.
 struct PointsView {
     const int4* idx;     // {k0_0, k0_1, k0_2, original index}, sorted by bin
@@ -55,7 +55,7 @@ struct PointsView {
     int64_t m;
     const float* w;      // [m][ws] kernel weights
     int ws;
-    int wd;              // weights per dimension in a row: J, or 8 (2-D strip layout, zero padded)
+    int wd;              // weights per dimension in a row: J, or 8 (strip layout, zero padded)
 };
 
 // ------------------------------------------------------------- FFT plans

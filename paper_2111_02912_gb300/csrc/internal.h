@@ -127,7 +127,7 @@ struct SortArgs {
     const float* kbtab;   // table mode: psi(l / tab_L) for l = 0 .. tab_n + 1 (zero from tab_n on), else null
     float tab_L;
     int tab_n;
-    // 2-D strip mode: the scatter also counts the strip units' hits, then the plan and fill
+    // strip mode: the scatter also counts the strip units' hits, then the plan and fill
     int strip, nunits;
     StripGeom sg;
     StripTables st;
@@ -143,7 +143,7 @@ cudaError_t launch_bin_scatter(const SortArgs& a, cudaStream_t s);   // records 
 // Deterministic order: ranks within each bin by original index (before the scatter; tmp is [M]
 // scratch).  Step 0 places the original indices, step 1 ranks them.
 cudaError_t launch_det_ranks(const SortArgs& a, int step, int* tmp, cudaStream_t s);
-// 2-D strip tables (kernels_strip.cu), after the scatter (which counts the hits per unit):
+// Strip tables (kernels_strip.cu), after the scatter (which counts the hits per unit):
 cudaError_t launch_strip_plan(const SortArgs& a, int step, cudaStream_t s);   // step 0: block totals; 1: offsets, items
 int strip_plan_blocks(int nunits);   // blocks of the plan launches
 int strip_plan_vals();               // per-block totals the plan keeps
@@ -338,7 +338,7 @@ struct SpreadArgs {
     KbPoly kb;
     float2* grid;         // [K...][C]
 };
-// 2-D strip spread (kernels_strip.cu): one warp per work item (a strip unit or a part of one).
+// Strip spread (kernels_strip.cu, 2-D and 3-D): one warp per work item (a strip unit or a part of one).
 struct StripArgs {
     PointsView pts;
     StripGeom g;

@@ -273,7 +273,7 @@ __global__ void k_bin_scatter(SortArgs a) {
             for (int j = 0; j < a.J; ++j) w[d * a.wd + j] = kb_psi(a.kb.a, a.kb.two_over_j, u0 - (float)j);
         for (int j = a.J; j < a.wd; ++j) w[d * a.wd + j] = 0.f;
     }
-    // 2-D strips: count the point as a hit of every unit its window reaches
+    // strips: count the point as a hit of every unit its window reaches
     if (a.strip) strip_point_units(a.sg, ix, [&](int u, int, int, int) { atomicAdd(a.st.hcount + u, 1); });
 }
 

@@ -85,7 +85,7 @@ struct nufft_plan_s {
     // bins
     int B[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, nbins = 1, cpb = 1, P = 1024, CCmax = 1;
     bool cell_spread = false;   // spread by the row-owner tile kernel (else the general kernel)
-    // 2-D strip spread: sort keys (bin, start row), strip units of NSL rows x kStripW columns
+    // strip spread (2-D and 3-D): strip units of NSL rows x kStripW columns of the last axis
     bool strip = false;
     bool deterministic = false;    // stable bin order and hit lists ordered by sorted point
     int kernel_mode = NUFFT_KERNEL_DIRECT, tab_L = 0, tab_n = 0;   // table mode: L samples per unit
@@ -132,8 +132,8 @@ struct nufft_plan_s {
     bool cap_pending = false;    // the same for a set_points recorded into capture cap_id
     unsigned long long cap_id = 0;
     float* d_pw = nullptr;   // [M_cap][ws] kernel weights of the sorted points
-    int ws = 4;              // D*J rounded up to a multiple of 4 (16 for the 2-D strips)
-    int wd = 6;              // weights per dimension in a row (J; 8 for the 2-D strips)
+    int ws = 4;              // D*J rounded up to a multiple of 4 (8 D for the strips)
+    int wd = 6;              // weights per dimension in a row (J; 8 for the strips)
     float c_hi[3] = {0, 0, 0}, c_lo[3] = {0, 0, 0};
     // workspace
     float2* d_G = nullptr;
@@ -407,7 +407,7 @@ size_t max_items(const nufft_plan_s& p, int64_t cap) {
     return n;
 }
 
-// Sort histogram entries: bins, or (bin, start row) keys for the 2-D strips.
+// Sort histogram entries: one per bin.
 int64_t sort_keys(const nufft_plan_s& p) { return (int64_t)p.nbins; }
 
 size_t strip_bytes(const nufft_plan_s& p) {
@@ -805,7 +805,7 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
     if (!gbuf) gbuf = p->d_G;
     if (!tbuf) tbuf = p->d_T;
     if (p->strip) {
-        // 2-D strips: every grid cell written once by its unit; y in sorted point-major order
+        // strips: every grid cell written once by its unit; y in sorted point-major order
         StripArgs ta{};
         ta.pts = PointsView{p->d_pidx, p->d_pfrac, p->M, p->d_pw, p->ws, p->wd};
         ta.g = strip_geom(*p);

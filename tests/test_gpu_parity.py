@@ -425,3 +425,27 @@ def test_kernel_mode_refused_by_the_allocation_free_forward():
     with pytest.raises(_abi.NufftError) as e:
         _abi.nufft_forward_noalloc(o, 100, om.data_ptr(), 1, x.data_ptr(), 0, y.data_ptr(), 0)
     assert e.value.status == _abi.NUFFT_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("name,shape,M,C,maps", [
+    ("dual_16_coils", (48, 40), 3000, 16, True),     # grad_x on the plan's second stream
+    ("dual_multi_image", (32, 24), 2000, 5, False),
+    ("single_stream_20_coils", (24, 40), 1500, 20, True),   # more than 16 coils with maps: one stream
+])
+def test_vjp_with_both_outputs_equals_each_output_alone(name, shape, M, C, maps):
+    """The VJP with both outputs (two streams on 2-D strip plans) gives bitwise the grad_omega of the
+    omega-only call and the grad_x of the x-only call (deterministic plan: one summation order)."""
+    import torch
+    seed = sum(map(ord, name))
+    case = make_case(shape, M, C, maps, seed=seed)
+    plan = _plan(case, deterministic=True)
+    X, S, V = (to_dev(case[k]) for k in ("x", "smaps", "v"))
+    go, gx = plan.vjp_omega_x(X, V, S)
+    go, gx = go.clone(), gx.clone()
+    go1 = plan.vjp_omega_x(X, V, S, need_x=False)[0].clone()
+    gx1 = plan.vjp_omega_x(X, V, S, need_omega=False)[1].clone()
+    torch.cuda.synchronize()
+    assert torch.equal(go, go1) and torch.equal(gx, gx1)
+    op = KBNufft(shape, case["omega"])
+    go_ref, gx_ref = jb.vjp_omega_x(op, case["x"], case["v"], case["smaps"])
+    assert rel(host(go), go_ref) < TOL_SAME and rel(host(gx), gx_ref) < TOL_SAME
