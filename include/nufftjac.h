@@ -127,6 +127,14 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
  * call's FFT passes. */
 int nufft_set_points(nufft_plan_t p, int64_t m, const float* omega, void* stream);
 
+/* Run the bin sort of the points last given to nufft_set_points now, on `stream`
+ * (forked to the plan's own stream and joined back before the call returns), instead
+ * of in the next call that needs them: for a caller that has omega on the device
+ * before the other inputs of the next call (e.g. while they are still being copied
+ * from the host) and orders that call after this stream.  Does nothing when the
+ * points are sorted already.  Same Appendix passage as nufft_set_points. */
+int nufft_sort_points(nufft_plan_t p, void* stream);
+
 /* y[C][M] = E x: forward NUFFT of each coil image (Sec. II-B, II-G). */
 int nufft_forward(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cfloat* smaps,
                   nufft_cfloat* y, void* stream);

@@ -22,7 +22,7 @@ NUFFT_KERNEL_DIRECT, NUFFT_KERNEL_TABLE = 0, 1
 KERNEL_MODES = {"direct": 0, "table": 1}
 
 EXPORTED = (
-    "nufft_default_opts", "nufft_plan", "nufft_set_points", "nufft_forward", "nufft_adjoint",
+    "nufft_default_opts", "nufft_plan", "nufft_set_points", "nufft_sort_points", "nufft_forward", "nufft_adjoint",
     "nufft_jvp_omega", "nufft_vjp_omega_x", "nufft_workspace_bytes", "nufft_get_info", "nufft_destroy",
     "nufft_status_string", "nufft_last_error", "nufft_launch_count", "nufft_profile_enable",
     "nufft_profile_read", "nufft_forward_noalloc",
@@ -69,6 +69,7 @@ def lib():
         L.nufft_default_opts.restype = None
         L.nufft_plan.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(nufft_opts), i64, vp, vp]
         L.nufft_set_points.argtypes = [vp, i64, vp, vp]
+        L.nufft_sort_points.argtypes = [vp, vp]
         L.nufft_forward.argtypes = [vp, i32, vp, vp, vp, vp]
         L.nufft_adjoint.argtypes = [vp, i32, vp, vp, vp, vp]
         L.nufft_jvp_omega.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
@@ -89,7 +90,7 @@ def lib():
         L.nufft_profile_enable.argtypes = [vp, i32]
         L.nufft_profile_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
-        for name in ("nufft_plan", "nufft_set_points", "nufft_forward", "nufft_adjoint", "nufft_jvp_omega",
+        for name in ("nufft_plan", "nufft_set_points", "nufft_sort_points", "nufft_forward", "nufft_adjoint", "nufft_jvp_omega",
                      "nufft_vjp_omega_x", "nufft_get_info", "nufft_profile_enable", "nufft_profile_read"):
             getattr(L, name).restype = i32
         _lib = L
@@ -122,6 +123,10 @@ def nufft_plan(opts, m, omega_ptr, stream=0):
 
 def nufft_set_points(plan, m, omega_ptr, stream=0):
     _check(lib().nufft_set_points(plan, int(m), omega_ptr, stream), "nufft_set_points")
+
+
+def nufft_sort_points(plan, stream=0):
+    _check(lib().nufft_sort_points(plan, stream), "nufft_sort_points")
 
 
 def nufft_forward(plan, C, x, smaps, y, stream=0):

@@ -1118,6 +1118,13 @@ int nufft_set_points(nufft_plan_t p, int64_t m, const float* omega, void* stream
     return do_set_points(p, m, omega, (cudaStream_t)stream);
 }
 
+int nufft_sort_points(nufft_plan_t p, void* stream) {
+    if (!p) return fail(NUFFT_ERR_INVALID_ARG, "plan is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    return finish_call(p, s, sort_rest(p, s));
+}
+
 int nufft_forward(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cfloat* smaps, nufft_cfloat* y,
                   void* stream) {
     int st;

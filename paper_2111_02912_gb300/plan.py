@@ -65,6 +65,10 @@ class Plan:
         self._omega = omega
         self.M = M
 
+    def sort_points(self):
+        """Sort the points of the last set_points now, on the current stream (else the next call does)."""
+        _abi.nufft_sort_points(self.handle, _stream())
+
     def _coils(self, x, smaps):
         if smaps is not None:
             return int(smaps.shape[0])

@@ -449,3 +449,28 @@ def test_vjp_with_both_outputs_equals_each_output_alone(name, shape, M, C, maps)
     op = KBNufft(shape, case["omega"])
     go_ref, gx_ref = jb.vjp_omega_x(op, case["x"], case["v"], case["smaps"])
     assert rel(host(go), go_ref) < TOL_SAME and rel(host(gx), gx_ref) < TOL_SAME
+
+
+def test_sort_points_on_another_stream_then_calls_on_the_main_stream():
+    """nufft_sort_points sorts now on the caller's stream; later calls ordered after it (an event)
+    need no sort of their own and give the same results; a second sort_points does nothing."""
+    import torch
+    case = make_case((32, 40), 2000, 4, True, seed=91)
+    plan = _plan(case)
+    X, S, V = (to_dev(case[k]) for k in ("x", "smaps", "v"))
+    y0 = plan.forward(X, S).clone()
+    go0, gx0 = (t.clone() for t in plan.vjp_omega_x(X, V, S))
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.set_points(to_dev(case["omega"]))
+        plan.sort_points()
+        plan.sort_points()
+        ev = torch.cuda.Event()
+        ev.record(side)
+    torch.cuda.current_stream().wait_event(ev)
+    y1 = plan.forward(X, S)
+    go1, gx1 = plan.vjp_omega_x(X, V, S)
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y1) and torch.equal(go0, go1)
+    assert rel(host(gx1), host(gx0)) < 1e-6
