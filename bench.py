@@ -640,6 +640,15 @@ def run_cgsense3d(args):
 
 
 # ------------------------------------------------------------------ batched uneven problems
+def config_picks(configs):
+    """How many problems the autotuner gave each configuration (a configuration: a tuple of fields)."""
+    picks = {}
+    for cfg in configs:
+        k = ",".join(str(f) for f in cfg) if cfg else "default"
+        picks[k] = picks.get(k, 0) + 1
+    return picks
+
+
 def batched_record(steps, warmup):
     """64 uneven problems: the captured-graph batch against the plain per-call path."""
     import torch
@@ -669,10 +678,7 @@ def batched_record(steps, warmup):
     bj.capture()
     with ClockSampler(torch.cuda.current_device()) as clk:
         ms_graph, _ = timed(bj.replay)
-    picks = {}
-    for it in bj.items:
-        k = "%s,%s,%s" % it.config if it.config else "default"
-        picks[k] = picks.get(k, 0) + 1
+    picks = config_picks(it.config for it in bj.items)
     rec = {"workload": "batched: 64 independent 2-D problems, side uniform over {64,...,384}, M uniform 4000-200000 "
                        "random-angle radial points (spokes of 2N), coils uniform 1-32; per problem set_points + "
                        "forward + vjp(grad_omega, grad_x); autotuned configuration; one CUDA graph over 4 streams",
@@ -682,7 +688,8 @@ def batched_record(steps, warmup):
            "plain_p50_ms": float(np.percentile(ms_plain, 50)), "plain_p99_ms": float(np.percentile(ms_plain, 99)),
            "speedup_vs_plain": sum(ms_plain) / sum(ms_graph), "steps": steps, "units_per_step": units,
            "points": sum(it.M for it in bj.items), "configs_picked": picks,
-           "config_candidates": "(spread kernel, bin shape, hits per strip part)", "gpu_launches_plain": launches_plain,
+           "config_candidates": "(spread kernel, bin shape, hits per strip part, forward gather lanes)",
+           "gpu_launches_plain": launches_plain,
            "l2": "inputs larger than L2"}
     return rec, clk.summary()
 

@@ -91,10 +91,17 @@ typedef struct {
                          table_density points per grid unit and read by linear interpolation (the
                          table interpolator of Sec. II-B / Sec. IV-A, for comparison; less accurate) */
     int table_density; /* NUFFT_KERNEL_TABLE: samples per grid unit, 16..65536 (0 -> 512) */
-    int reserved[1];
+    int gather_variant; /* lanes of the forward gather: NUFFT_GATHER_AUTO (0), _PAIRS, _QUADS */
 } nufft_opts;
 
 enum { NUFFT_KERNEL_DIRECT = 0, NUFFT_KERNEL_TABLE = 1 };
+
+/* Forward gather (interpolation, Appendix step 3) lane layouts (nufft_opts.gather_variant), all
+ * computing the same sums: a lane owns two adjacent coils (PAIRS: one 16-byte load per tap) or
+ * four (QUADS: one 32-byte load per tap, twice the points per warp; for C a multiple of 4 from 8
+ * on, else pairs).  AUTO takes quads for the 2-D forward with C a multiple of 4 from 16 on, where
+ * they measured faster, and pairs elsewhere.  The JVP and VJP gathers always use pairs. */
+enum { NUFFT_GATHER_AUTO = 0, NUFFT_GATHER_PAIRS = 1, NUFFT_GATHER_QUADS = 2 };
 
 /* Adjoint spread kernels (nufft_opts.spread_variant), all computing the transpose of the
  * interpolation (Sec. II-D); AUTO takes STRIPS where it applies, else TILES, else GENERAL.

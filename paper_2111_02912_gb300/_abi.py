@@ -20,6 +20,7 @@ NUFFT_SPREAD_AUTO, NUFFT_SPREAD_STRIPS, NUFFT_SPREAD_TILES, NUFFT_SPREAD_GENERAL
 SPREAD_VARIANTS = {"auto": 0, "strips": 1, "tiles": 2, "general": 3}
 NUFFT_KERNEL_DIRECT, NUFFT_KERNEL_TABLE = 0, 1
 KERNEL_MODES = {"direct": 0, "table": 1}
+GATHER_VARIANTS = {"auto": 0, "pairs": 1, "quads": 2}
 
 EXPORTED = (
     "nufft_default_opts", "nufft_plan", "nufft_set_points", "nufft_sort_points", "nufft_forward", "nufft_adjoint",
@@ -37,7 +38,7 @@ class nufft_opts(ctypes.Structure):
                 ("J", ctypes.c_int), ("beta", ctypes.c_double), ("max_coils", ctypes.c_int),
                 ("bin_size", ctypes.c_int * 3), ("deterministic", ctypes.c_int), ("spread_variant", ctypes.c_int),
                 ("strip_part", ctypes.c_int), ("kernel_mode", ctypes.c_int),
-                ("table_density", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("table_density", ctypes.c_int), ("gather_variant", ctypes.c_int)]
 
 
 class nufft_plan_info(ctypes.Structure):

@@ -13,9 +13,9 @@ a batch:
 The autotuner times one step per candidate configuration on the device and keeps
 the fastest, cached per (shape, coils, log2 M) class.  A configuration is the
 adjoint spread kernel (register strips or shared-memory tiles), the bin shape of
-the sort (the locality of the gathers' tap reads, and the tile of the tile spread)
-and, for the strips, the hits one warp adds before a unit is split into parts (the
-work per warp).
+the sort (the locality of the gathers' tap reads, and the tile of the tile spread),
+for the strips the hits one warp adds before a unit is split into parts (the
+work per warp), and the forward gather's lanes (coil pairs or quads).
 """
 import math
 
@@ -23,17 +23,18 @@ import torch
 
 from .plan import Plan
 
-# (spread kernel, bin shape, strip part); the tile kernel ignores the strip part
+# (spread kernel, bin shape, strip part, forward gather lanes); the tile kernel ignores the strip part
 CONFIG_CANDIDATES_2D = (
-    ("strips", (16, 16), 64), ("strips", (16, 16), 32), ("strips", (16, 16), 128), ("strips", (32, 32), 64),
-    ("tiles", (16, 16), 0), ("tiles", (16, 32), 0),
+    ("strips", (16, 16), 64, "auto"), ("strips", (16, 16), 32, "auto"), ("strips", (16, 16), 128, "auto"),
+    ("strips", (32, 32), 64, "auto"), ("tiles", (16, 16), 0, "auto"), ("tiles", (16, 32), 0, "auto"),
+    ("strips", (16, 16), 64, "pairs"), ("strips", (16, 16), 64, "quads"),
 )
 BIN_CANDIDATES_2D = tuple(sorted({c[1] for c in CONFIG_CANDIDATES_2D}))
 
 
 def plan_for(item, config):
-    spread, bins, part = config
-    return Plan(item.shape, item.om, max_coils=item.C, bin_size=bins, spread=spread, strip_part=part)
+    spread, bins, part, gather = config
+    return Plan(item.shape, item.om, max_coils=item.C, bin_size=bins, spread=spread, strip_part=part, gather=gather)
 
 
 class Autotuner:

@@ -89,6 +89,7 @@ struct nufft_plan_s {
     bool strip = false;
     bool deterministic = false;    // stable bin order and hit lists ordered by sorted point
     int kernel_mode = NUFFT_KERNEL_DIRECT, tab_L = 0, tab_n = 0;   // table mode: L samples per unit
+    int gather_variant = NUFFT_GATHER_AUTO;
     float* d_kbtab = nullptr;      // [tab_n + 2] psi(l / tab_L), zero from tab_n on
     int2* d_hits_tmp = nullptr;    // [hit_cap] the fill's list before ordering (deterministic only)
     int NSL = 2, SR0 = 2, SR1 = 1, nunits = 0, strip_P = 64, strip_slots = 0, ncg_max = 1;
@@ -352,6 +353,9 @@ int validate_opts(const nufft_opts* o, nufft_plan_s& p) {
     }
     if (ak > 1e-9 * sum) return fail(NUFFT_ERR_UNSUPPORTED, "beta too large for the kernel power series");
     p.kb.two_over_j = (float)(2.0 / p.J);
+    p.gather_variant = o->gather_variant;
+    if (p.gather_variant < NUFFT_GATHER_AUTO || p.gather_variant > NUFFT_GATHER_QUADS)
+        return fail(NUFFT_ERR_INVALID_ARG, "unknown gather_variant");
     p.kernel_mode = o->kernel_mode;
     if (p.kernel_mode != NUFFT_KERNEL_DIRECT && p.kernel_mode != NUFFT_KERNEL_TABLE)
         return fail(NUFFT_ERR_INVALID_ARG, "kernel_mode must be NUFFT_KERNEL_DIRECT or NUFFT_KERNEL_TABLE");
@@ -943,12 +947,16 @@ int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cu
     return NUFFT_OK;
 }
 
-// The 2-D forward gather with C a multiple of 4 from 16 on: a lane owns four adjacent coils
-// (32-byte loads, twice the points per warp).  Measured on 640^2 / 16 coils: 23.0 -> 22.0 us; the
-// VJP kinds (40.1 -> 46.5 us: half the resident warps) and the 3-D gathers (1.35 -> 1.64 ms on
-// 8 coils) lose with it.
-void forward_quads(GatherArgs& g) {
-    if (g.D == 2 && g.C % 4 == 0 && g.C >= 16 && g.C <= 128) {
+// The forward gather on coil quads: a lane owns four adjacent coils (32-byte loads, twice the
+// points per warp).  AUTO takes them for the 2-D forward with C a multiple of 4 from 16 on (640^2 /
+// 16 coils: 23.0 -> 22.0 us); the VJP kinds (40.1 -> 46.5 us: half the resident warps) and the 3-D
+// gathers (1.35 -> 1.64 ms on 8 coils) lose with them.  QUADS takes them wherever C is a multiple
+// of 4 from 8 on; PAIRS never.
+void forward_quads(const nufft_plan_s* p, GatherArgs& g) {
+    const bool quads = p->gather_variant == NUFFT_GATHER_QUADS
+                           ? (g.C % 4 == 0 && g.C >= 8)
+                           : (p->gather_variant == NUFFT_GATHER_AUTO && g.D == 2 && g.C % 4 == 0 && g.C >= 16);
+    if (quads && g.C <= 128) {
         g.W = 4;
         g.G = pow2_ceil(g.C / 4);
         g.lgG = ilog2(g.G);
@@ -1137,7 +1145,7 @@ int nufft_forward(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cflo
     if ((st = forward_grids(p, C, 1, 1, (const float2*)x, (const float2*)smaps, s))) return st;
     if ((st = sort_join(p, s))) return st;
     GatherArgs g = gather_args(p, C, 1, 1);
-    forward_quads(g);
+    forward_quads(p, g);
     g.y = (float2*)y;
     const int cpl = gather_cpl(g);
     return finish_call(p, s, launch(p, PK_GATHER_FWD, s, [&] { return launch_gather(GM_FWD, g, cpl, s); }));
@@ -1483,7 +1491,7 @@ extern "C" int nufft_forward_noalloc(const nufft_opts* o, int64_t m, const float
     if (m == 0) return NUFFT_OK;
     if ((st = forward_grids(&p, C, 1, 1, (const float2*)x, (const float2*)smaps, s))) return st;
     GatherArgs g = gather_args(&p, C, 1, 1);
-    forward_quads(g);
+    forward_quads(&p, g);
     g.y = (float2*)y;
     const int cpl = gather_cpl(g);
     return launch(&p, PK_GATHER_FWD, s, [&] { return launch_gather(GM_FWD, g, cpl, s); });

@@ -29,7 +29,7 @@ def _stream():
 
 class Plan:
     def __init__(self, shape, omega, J=6, sigma=2.0, beta=None, max_coils=1, bin_size=None, spread="auto",
-                 deterministic=False, strip_part=0, kernel_mode="direct", table_density=0):
+                 deterministic=False, strip_part=0, kernel_mode="direct", table_density=0, gather="auto"):
         self.shape = tuple(int(n) for n in shape)
         self.D = len(self.shape)
         opts = _abi.nufft_default_opts(self.D, self.shape)
@@ -45,6 +45,7 @@ class Plan:
         opts.strip_part = int(strip_part)
         opts.kernel_mode = _abi.KERNEL_MODES[kernel_mode]
         opts.table_density = int(table_density)
+        opts.gather_variant = _abi.GATHER_VARIANTS[gather]
         self.max_coils = int(max_coils)
         self._omega = omega
         self.M = int(omega.shape[1])

@@ -108,6 +108,14 @@ def test_workspace_bytes_scale_with_coils_and_grid(abi):
     assert abi.nufft_workspace_bytes(o, 51200, 16) == b16      # C overrides max_coils
 
 
+def test_invalid_gather_variant_is_rejected(abi):
+    o = abi.nufft_default_opts(2, (64, 64))
+    o.gather_variant = 3
+    with pytest.raises(abi.NufftError) as e:
+        abi.nufft_plan(o, 0, None)
+    assert e.value.status == abi.NUFFT_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("mode,density", [(2, 0), (-1, 0), (1, 8), (1, 70000)])
 def test_invalid_kernel_mode_or_table_density_is_rejected(abi, mode, density):
     o = abi.nufft_default_opts(2, (64, 64))

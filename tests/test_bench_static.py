@@ -35,3 +35,13 @@ def _undefined(path):
 @pytest.mark.parametrize("path", FILES)
 def test_every_name_read_is_defined(path):
     assert _undefined(path) == []
+
+
+def test_config_picks_counts_every_candidate_shape():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2111_02912_gb300.batch import CONFIG_CANDIDATES_2D
+    picks = bench.config_picks(list(CONFIG_CANDIDATES_2D) + [CONFIG_CANDIDATES_2D[0], None])
+    assert sum(picks.values()) == len(CONFIG_CANDIDATES_2D) + 2
+    assert picks[",".join(str(f) for f in CONFIG_CANDIDATES_2D[0])] == 2 and picks["default"] == 1

@@ -474,3 +474,20 @@ def test_sort_points_on_another_stream_then_calls_on_the_main_stream():
     torch.cuda.synchronize()
     assert torch.equal(y0, y1) and torch.equal(go0, go1)
     assert rel(host(gx1), host(gx0)) < 1e-6
+
+
+@pytest.mark.parametrize("shape,M,C,gather", [
+    ((32, 40), 1500, 8, "quads"), ((32, 40), 1500, 12, "quads"), ((32, 40), 1500, 16, "pairs"),
+    ((32, 40), 1500, 24, "auto"), ((16, 20, 12), 1500, 8, "quads"), ((64,), 700, 8, "quads"),
+])
+def test_forward_gather_variants_match_the_oracle(shape, M, C, gather):
+    """nufft_opts.gather_variant: coil pairs or quads in the forward gather give the same operator."""
+    import torch
+    seed = sum(map(ord, gather)) + C
+    case = make_case(shape, M, C, True, seed=seed)
+    plan = _plan(case, gather=gather)
+    X, S = to_dev(case["x"]), to_dev(case["smaps"])
+    y = plan.forward(X, S)
+    torch.cuda.synchronize()
+    y_ref = jb.sense_forward(KBNufft(shape, case["omega"]), case["x"], case["smaps"])
+    assert rel(host(y), y_ref) < TOL_SAME and max_rel(host(y), y_ref) < TOL_SAME
