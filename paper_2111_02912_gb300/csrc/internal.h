@@ -109,7 +109,8 @@ struct SortArgs {
     int nbins, P;         // P: spread candidates per work item
     float c_hi[kMaxDim], c_lo[kMaxDim];  // K/(2 pi) as a float pair
     int* kcount;      // [nbins]      points per bin; zero before the sort, cleared again by the bin scan
-    int* local;       // [M]          rank among the points of the same bin
+    int* local;       // [M]          rank among the points of the same bin; the bin scatter then
+                      //              replaces it by the point's sorted position
     int* keyid;       // [M]
     int* offsets;     // [nbins + 1]  first sorted point of each bin
     int* item_off;    // [nbins + 1]  first spread work item of each tile
@@ -351,8 +352,8 @@ struct StripArgs {
     int* counters;        // [slots][ncg], zero between calls
 };
 cudaError_t launch_spread_strips(const StripArgs& a, cudaStream_t s);
-// ys = y[c][idx[i].w] in sorted point order, in the strip layout [ncg][M][cpt].
-cudaError_t launch_permute_y_strips(const int4* idx, const float2* y, float2* ys, int64_t M, int C, int cpt,
+// ys[sorted position pos[o] of point o] = y[c][o], in the strip layout [ncg][M][cpt].
+cudaError_t launch_permute_y_strips(const int* pos, const float2* y, float2* ys, int64_t M, int C, int cpt,
                                     cudaStream_t s);
 cudaError_t launch_spread(const SpreadArgs& a, int cpl, cudaStream_t s, size_t smem);
 cudaError_t launch_zero_heavy_tiles(const SpreadArgs& a, cudaStream_t s);

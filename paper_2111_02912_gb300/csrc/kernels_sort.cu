@@ -261,6 +261,7 @@ __global__ void k_bin_scatter(SortArgs a) {
     int64_t key;
     point_record(a, i, ix, fr, key);
     const int dst = a.offsets[a.keyid[i]] + a.local[i];
+    a.local[i] = dst;   // the inverse of the sort permutation, for reordering coil values
     a.pidx[dst] = ix;
     a.pfrac[dst] = fr;
     // the D*J kernel weights, evaluated once here and read by every gather and spread

@@ -494,34 +494,36 @@ cudaError_t launch_spread_strips(const StripArgs& a, cudaStream_t s) {
     return a.g.D == 3 ? strips_d<3>(a, s) : strips_d<2>(a, s);
 }
 
-// Coil values in sorted point order, in the strip layout [C / cpt][M][cpt].
-__global__ void k_permute_y_strips(const int4* __restrict__ idx, const float2* __restrict__ y,
-                                   float2* __restrict__ ys, int64_t M, int C, int cpt) {
+// Coil values in sorted point order, in the strip layout [C / cpt][M][cpt], from y [C][M] in the
+// caller's point order.  A block takes kPermPts consecutive points of the caller's order: it reads
+// each coil's values of those points as one coalesced row segment into shared memory, then writes
+// every point's coil values as contiguous runs at the point's sorted position pos[o] (the bin
+// scatter leaves it there).  Both the reads and the writes are whole sectors.
+constexpr int kPermPts = 32;
+__global__ void __launch_bounds__(256) k_permute_y_strips(const int* __restrict__ pos, const float2* __restrict__ y,
+                                                          float2* __restrict__ ys, int64_t M, int C, int cpt) {
     pdl_wait();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M) return;
-    const int64_t o = idx[i].w;
-    int c = 0;
-    for (; c + 4 <= C; c += 4) {   // four independent loads in flight
-        float2 v[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = __ldg(y + (int64_t)(c + k) * M + o);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int cc = c + k, grp = cc / cpt;
-            ys[((int64_t)grp * M + i) * cpt + (cc - grp * cpt)] = v[k];
-        }
-    }
-    for (; c < C; ++c) {
+    extern __shared__ float2 tp[];   // [C][kPermPts + 1]
+    const int64_t o0 = (int64_t)blockIdx.x * kPermPts;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int np = (int)(M - o0 < kPermPts ? M - o0 : kPermPts);
+    for (int c = warp; c < C; c += nwarps)
+        if (lane < np) tp[c * (kPermPts + 1) + lane] = __ldg(y + (int64_t)c * M + o0 + lane);
+    __syncthreads();
+    for (int f = threadIdx.x; f < np * C; f += blockDim.x) {
+        const int q = f / C, c = f - q * C;   // consecutive threads: consecutive coils of one point
+        const int64_t i = __ldg(pos + o0 + q);
         const int grp = c / cpt;
-        ys[((int64_t)grp * M + i) * cpt + (c - grp * cpt)] = __ldg(y + (int64_t)c * M + o);
+        ys[((int64_t)grp * M + i) * cpt + (c - grp * cpt)] = tp[c * (kPermPts + 1) + q];
     }
 }
 
-cudaError_t launch_permute_y_strips(const int4* idx, const float2* y, float2* ys, int64_t M, int C, int cpt,
+cudaError_t launch_permute_y_strips(const int* pos, const float2* y, float2* ys, int64_t M, int C, int cpt,
                                     cudaStream_t s) {
     if (M == 0) return cudaSuccess;
-    (void)launch_pdl(k_permute_y_strips, (unsigned)((M + 255) / 256), 256, 0, s, idx, y, ys, M, C, cpt);
+    const size_t smem = (size_t)C * (kPermPts + 1) * sizeof(float2);
+    (void)launch_pdl(k_permute_y_strips, (unsigned)((M + kPermPts - 1) / kPermPts), 256, smem, s, pos, y, ys, M, C,
+                     cpt);
     return cudaGetLastError();
 }
 

@@ -113,7 +113,7 @@ struct nufft_plan_s {
     int* d_tile_nbr = nullptr;
     int* d_nitems = nullptr;
     int4* d_items = nullptr;
-    int* d_local = nullptr;
+    int* d_local = nullptr;   // [M_cap] rank within the bin, then (after the scatter) sorted position
     int* d_keyid = nullptr;
     int4* d_pidx = nullptr;
     float4* d_pfrac = nullptr;
@@ -825,7 +825,7 @@ int adjoint_impl(nufft_plan_s* p, int C, const float2* y, const float2* smaps, f
             ta.y = ysorted;
         } else {
             if ((st = launch(p, PK_PERMUTE_Y, s,
-                             [&] { return launch_permute_y_strips(p->d_pidx, y, p->d_ys, p->M, C, cpt, s); })))
+                             [&] { return launch_permute_y_strips(p->d_local, y, p->d_ys, p->M, C, cpt, s); })))
                 return st;
             ta.y = p->d_ys;
         }
