@@ -96,7 +96,6 @@ struct StripTables {
     int* nitems;      // [0] items, [1] hits per part
     int P;            // hits per part (doubled until the split parts fit the slots), a power of two
     int slots;        // partial-sum slots
-    int* work;        // [2 per coil group] spread work counter and warps finished, zero between calls
     int* partial_sums;  // [plan blocks][plan values] per-block totals of the plan
 };
 

@@ -98,7 +98,6 @@ struct nufft_plan_s {
     int* d_counters = nullptr;     // [strip_slots][ncg_max], zero between calls
     int* d_hcount = nullptr;       // [nunits] hits per strip unit
     int* d_hcur = nullptr;         // [nunits] fill cursors
-    int* d_work = nullptr;         // [2 ncg_max] per coil group: spread work counter, warps finished
     int* d_plan_sums = nullptr;    // per-block totals of the strip plan
     int* d_hoff = nullptr;         // [nunits + 1]
     int2* d_hits = nullptr;        // [hit_cap] strip hit lists
@@ -235,7 +234,7 @@ void free_plan(nufft_plan_s* p) {
     cudaFree(p->d_pw); cudaFree(p->d_om);
     cudaFree(p->d_G); cudaFree(p->d_T);
     cudaFree(p->d_partial); cudaFree(p->d_counters); cudaFree(p->d_ys); cudaFree(p->d_hcount); cudaFree(p->d_hoff);
-    cudaFree(p->d_hits); cudaFree(p->d_splits); cudaFree(p->d_hcur); cudaFree(p->d_work); cudaFree(p->d_plan_sums);
+    cudaFree(p->d_hits); cudaFree(p->d_splits); cudaFree(p->d_hcur); cudaFree(p->d_plan_sums);
     cudaFree(p->d_hits_tmp);
     if (p->aux) cudaStreamDestroy(p->aux);
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
@@ -474,7 +473,6 @@ StripTables strip_tables(const nufft_plan_s& p) {
     StripTables t{};
     t.hcount = p.d_hcount;
     t.hcur = p.d_hcur;
-    t.work = p.d_work;
     t.partial_sums = p.d_plan_sums;
     t.hoff = p.d_hoff;
     t.hits = p.d_hits;
@@ -1084,7 +1082,6 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
             cudaMalloc(&p->d_counters, nslot * sizeof(int)) != cudaSuccess ||
             cudaMalloc(&p->d_hcount, (size_t)p->nunits * sizeof(int)) != cudaSuccess ||
             cudaMalloc(&p->d_hcur, (size_t)p->nunits * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&p->d_work, 2 * (size_t)p->ncg_max * sizeof(int)) != cudaSuccess ||
             cudaMalloc(&p->d_plan_sums, (size_t)strip_plan_blocks(p->nunits) * strip_plan_vals() * sizeof(int)) !=
                 cudaSuccess ||
             cudaMalloc(&p->d_hoff, (size_t)(p->nunits + 1) * sizeof(int)) != cudaSuccess ||
@@ -1092,7 +1089,6 @@ int nufft_plan(nufft_plan_t* out, const nufft_opts* o, int64_t m, const float* o
             return oom("strip partial sums");
         cudaMemset(p->d_counters, 0, nslot * sizeof(int));
         cudaMemset(p->d_hcount, 0, (size_t)p->nunits * sizeof(int));
-        cudaMemset(p->d_work, 0, 2 * (size_t)p->ncg_max * sizeof(int));
     }
     workspace_elems(*p, p->G_elems, p->T_elems);
     if (cudaMalloc(&p->d_G, p->G_elems * sizeof(float2)) != cudaSuccess ||
