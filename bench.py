@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving: length of the arrival process")
     ap.add_argument("--serve-fuse", type=int, default=8,
                     help="serving: most same-problem reconstructions fused into one job (1: no fusion)")
+    ap.add_argument("--small3d", action="store_true",
+                    help="cgsense3d: the same problem at half the side (64x64x48, 250,000 points), for profiling")
     ap.add_argument("--no-graph", action="store_true",
                     help="radial320: time the eager per-call step only (default: replay the step from a CUDA graph)")
     return ap.parse_args()
@@ -99,18 +101,54 @@ def make_inputs():
     return w
 
 
-def touched_cells(omega, K, J):
-    """Grid cells inside some sample's J-tap window (algorithmic grid footprint U)."""
+def touched_cells(omega, K, J, chunk=65536):
+    """Grid cells inside some sample's J-tap window (algorithmic grid footprint U), marked in a
+    boolean grid a chunk of samples at a time."""
     D, M = omega.shape
-    starts = []
-    for d in range(D):
-        t = omega[d].astype(np.float64) * K[d] / (2 * np.pi)
-        starts.append(np.floor(t - J / 2.0).astype(np.int64) + 1)
-    lin = np.zeros((M, 1), dtype=np.int64)
-    for d in range(D):
-        k = np.mod(starts[d][:, None] + np.arange(J)[None, :], K[d])
-        lin = (lin[:, :, None] * K[d] + k[:, None, :]).reshape(M, -1)
-    return int(np.unique(lin).size)
+    hit = np.zeros(int(np.prod(K)), dtype=bool)
+    for m0 in range(0, M, chunk):
+        om = omega[:, m0:m0 + chunk]
+        lin = np.zeros((om.shape[1], 1), dtype=np.int64)
+        for d in range(D):
+            t = om[d].astype(np.float64) * K[d] / (2 * np.pi)
+            start = np.floor(t - J / 2.0).astype(np.int64) + 1
+            k = np.mod(start[:, None] + np.arange(J)[None, :], K[d])
+            lin = (lin[:, :, None] * K[d] + k[:, None, :]).reshape(om.shape[1], -1)
+        hit[lin.ravel()] = True
+    return int(hit.sum())
+
+
+# Nominal L1 data return of one SM per cycle (32 lanes x 4 bytes) and the SM count: the 3-D gathers
+# read J^D taps x ch channels per point through L1, far more than they move from HBM.
+L1_BYTES_PER_CYCLE_SM = 128
+SM_COUNT = 152
+
+
+def gather3d_roofline(prof, omega, K, C, J, sm_mhz):
+    """HBM and L1 figures of the 3-D forward and VJP gathers from the library's per-kernel events:
+    HBM algorithmic bytes U ch 8 + M D 4 + M C 8 (+ M D 4 for grad_omega), L1 tap bytes M J^D ch 8
+    against SM_COUNT x L1_BYTES_PER_CYCLE_SM x the median SM clock."""
+    D, M = omega.shape
+    U = touched_cells(omega, K, J)
+    hbm, hbm_src = peaks()
+    l1_peak = SM_COUNT * L1_BYTES_PER_CYCLE_SM * sm_mhz * 1e6 / 1e9
+    out = {"U_cells": U, "l1_peak_gbs": round(l1_peak, 1),
+           "l1_peak_source": "derived: %d SMs x %d B/cycle x %.0f MHz (median SM clock of the run)" %
+                             (SM_COUNT, L1_BYTES_PER_CYCLE_SM, sm_mhz),
+           "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)"}
+    for kind, ch, extra in (("gather_fwd", C, 0), ("gather_vjp", C * D, M * D * 4)):
+        if kind not in prof or prof[kind][0] == 0:
+            continue
+        launches, ms = prof[kind]
+        sec = ms / 1e3 / launches
+        b_hbm = U * ch * 8 + M * D * 4 + M * C * 8 + extra
+        b_l1 = M * J ** D * ch * 8
+        out[kind] = {"launches": launches, "us_per_launch": round(sec * 1e6, 1),
+                     "hbm_bytes_per_launch": b_hbm, "hbm_gbs": round(b_hbm / sec / 1e9, 1),
+                     "hbm_frac": round(b_hbm / sec / 1e9 / hbm, 4),
+                     "l1_tap_bytes_per_launch": b_l1, "l1_gbs": round(b_l1 / sec / 1e9, 1),
+                     "l1_frac": round(b_l1 / sec / 1e9 / l1_peak, 4)}
+    return out
 
 
 def algorithmic_bytes(w, info):
@@ -561,7 +599,7 @@ def cgsense_units(M, C, D, K):
     return M * C * ((4 * K) + (3 * K + 1)) + M * C * D * (2 * K + 1)
 
 
-def cgsense_record(steps, warmup):
+def cgsense_record(steps, warmup, name="radial3d"):
     """The 3-D CG-SENSE loss-gradient step: (JSON fields, value, ms per step, clocks)."""
     import torch
 
@@ -569,7 +607,7 @@ def cgsense_record(steps, warmup):
     from paper_2111_02912_gb300.autograd import NufftOperator, cg_sense_unrolled, nufft
     from paper_2111_02912_gb300.workloads import workload
     dev = torch.device("cuda", torch.cuda.current_device())
-    w = workload("radial3d")
+    w = workload(name)
     C, M, D = w["C"], w["omega"].shape[1], 3
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     om = t(w["omega"]).requires_grad_(True)
@@ -609,31 +647,36 @@ def cgsense_record(steps, warmup):
     prof = op.plan.profile_read()
     op.plan.profile_enable(False)
     units = cgsense_units(M, C, D, CG_ITERS)
-    rec = {"workload": "cgsense3d: 128x128x96 image, 8 coils, 2,000,000 points (8000 3-D radial spokes x 250, "
+    clocks = clk.summary()
+    shape, spokes, reads = w["shape"], w["omega"].shape[1] // (250 if name == "radial3d" else 125), \
+        250 if name == "radial3d" else 125
+    rec = {"workload": "cgsense3d: %dx%dx%d image, %d coils, %d points (%d 3-D radial spokes x %d, "
                        "random-walk perturbed); loss = ||x_K - x||^2, x_K = %d unrolled CG-SENSE iterations on "
                        "(E'E + lam I) x = E'y, lam = 1e-3 M; backward with per-iteration recomputation; gradient "
-                       "w.r.t. omega (D = 3)" % CG_ITERS,
+                       "w.r.t. omega (D = 3)" % (shape[0], shape[1], shape[2], C, M, spokes, reads, CG_ITERS),
            "value": units / (float(np.mean(ms)) / 1e3), "unit": UNIT, "ms_per_step": float(np.mean(ms)),
            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)), "steps": steps,
            "units_per_step": units, "peak_device_bytes": int(torch.cuda.max_memory_allocated()),
            "plan_workspace_bytes": int(op.plan.info().workspace_bytes), "gpu_launches": n1 - n0,
            "l2": "inputs larger than L2",
            "kernels_one_step": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()}}
-    return rec, clk.summary()
+    rec["gather_roofline"] = gather3d_roofline(prof, w["omega"], [2 * n for n in shape], C, 6,
+                                               clocks["sm_mhz"] if clocks else 2070.0)
+    return rec, clocks
 
 
 def run_cgsense3d(args):
     ws, rank, local = dist_env()
     import torch
     torch.cuda.set_device(local)
-    rec, clocks = cgsense_record(args.steps, max(3, args.warmup))
+    rec, clocks = cgsense_record(args.steps, max(3, args.warmup), "radial3d_small" if args.small3d else "radial3d")
     line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": rec["ms_per_step"], "p50_ms": rec["p50_ms"],
             "p99_ms": rec["p99_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64 (fp32 complex)",
             "data": "synthetic (seeded 3-D radial with random walk, ellipsoid phantom, Gaussian-bump maps)",
             "config": {k: rec[k] for k in ("workload", "units_per_step", "l2", "peak_device_bytes",
-                                           "plan_workspace_bytes", "kernels_one_step")},
+                                           "plan_workspace_bytes", "kernels_one_step", "gather_roofline")},
             "gpu_launches": rec["gpu_launches"], "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))

@@ -106,6 +106,8 @@ def workload(name, scale=1.0):
     small64   : 64x64 i.i.d. image, 1 coil, M=4096 uniform omega (2-D)
     radial320 : 320x320 image, 16 Gaussian-bump coils, 80 golden-angle spokes x 640
     radial3d  : 128x128x96 ellipsoid phantom, 8 coils, 8000 perturbed 3-D spokes x 250
+    radial3d_small : the same at half the side (64x64x48, 2000 spokes x 125: the same points per
+                grid cell), for profiling the 3-D kernels on a few hundred MB
     spoke40   : 40x40 image with random phase, 8 coils, one 80-point spoke through the centre
     """
     if name == "small64":
@@ -124,6 +126,12 @@ def workload(name, scale=1.0):
         n_spokes = max(1, int(round(8000 * scale)))
         return dict(shape=shape, x=ellipsoid_phantom(g, shape), smaps=gaussian_bump_maps(shape, 8),
                     omega=radial_3d(g, n_spokes, 250), C=8)
+    if name == "radial3d_small":
+        g = rng(5)
+        shape = (64, 64, 48)
+        n_spokes = max(1, int(round(2000 * scale)))
+        return dict(shape=shape, x=ellipsoid_phantom(g, shape), smaps=gaussian_bump_maps(shape, 8),
+                    omega=radial_3d(g, n_spokes, 125), C=8)
     if name == "spoke40":
         g = rng(3)
         shape = (40, 40)
