@@ -24,7 +24,9 @@
 // n_in nonzero positions of its input lines; INV_MID keeps the n_out cropped
 // positions; INV_LAST crops, stages the line in shared memory, then applies
 // the scaling and conj(s_c) and sums the tile's coils with loads and stores
-// coalesced along the image row.
+// coalesced along the image row (with pair_add, the two coil chunks of a row
+// each add their sum into the image that INV_MID cleared: x = 0 + a + b has the
+// same bits in either order, so the result does not depend on which comes first).
 #pragma once
 #include "fft_dft.cuh"
 #include "internal.h"
@@ -53,7 +55,9 @@ __device__ __forceinline__ void image_row_factors(const ImageSide& im, int64_t b
 // few bytes of spill (measured on the 640-point passes: FWD_MID 37.6 -> 31.5 us, INV_MID 26.4 ->
 // 22.4 us against 128 registers at two blocks per SM).  Other sizes keep 128: on the 400-point
 // passes (320-thread blocks) 80 registers cost FWD_FIRST 24.5 -> 28.3 us and FWD_MID 17.3 -> 19.0
-// us.  The coil-summing INV_LAST runs 512-thread blocks and keeps 128 as well.
+// us.  The coil-summing INV_LAST takes 8 coils per block as well when its two chunks add into the
+// image (9..16 coils: 640 blocks in 1.4 waves against 320 one-per-SM blocks of 16 coils in 2.1);
+// with more coils it runs 512-thread blocks of 16 at one block per SM.
 // Half-length pruning fixed at compile time (HALF: n_in = L / 2 on the forward side, n_out = L / 2 on
 // the inverse side, i.e. sigma = 2).  Then the kept positions p < L/4 or p >= 3L/4 are whole phase-1
 // registers n1 (p = L2 n1 + n2, L1 % 4 == 0) on the forward side and whole phase-2 outputs k2
@@ -65,8 +69,14 @@ __host__ __device__ constexpr bool fft2_half_applies() {
 }
 
 template <int L1, int L2, PassKind KIND, bool HALF>
-__global__ void __maxnreg__((KIND == PASS_INV_LAST || L2 != 32) ? 128 : 80) k_line_fft2(LinePass a) {
+__global__ void __maxnreg__(L2 != 32 ? 128 : 80) k_line_fft2(LinePass a) {
     pdl_wait();
+    if (KIND == PASS_INV_MID && a.clear) {   // the image the next pass's two coil chunks add into
+        const int64_t nthr = (int64_t)gridDim.x * gridDim.y * blockDim.x;
+        for (int64_t i = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x; i < a.nclear;
+             i += nthr)
+            a.clear[i] = make_float2(0.f, 0.f);
+    }
     constexpr int DIR = (KIND == PASS_FWD_FIRST || KIND == PASS_FWD_MID) ? -1 : 1;
     constexpr int L = L1 * L2;
     constexpr bool FH = HALF && DIR < 0 && fft2_half_applies<L1, L2, KIND>();   // forward: n1 kept iff
@@ -301,7 +311,9 @@ __global__ void __maxnreg__((KIND == PASS_INV_LAST || L2 != 32) ? 128 : 80) k_li
                         for (int q = 0; q < 8; ++q)
                             if (l0 + q < ncoil) sum = cadd(sum, cmulc(buf[(lb * TS + l0 + q) * LP + e], m[q]));
                     }
-                    xo[bb * nlast + e] = cscale(sum, rs * __ldg(deap_last + e));
+                    const float2 xv = cscale(sum, rs * __ldg(deap_last + e));
+                    if (a.pair_add) atomicAdd(xo + bb * nlast + e, xv);   // 2 adds onto 0: order-free
+                    else xo[bb * nlast + e] = xv;
                 }
             }
         } else {

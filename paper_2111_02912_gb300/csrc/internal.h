@@ -235,6 +235,10 @@ struct LinePass {
     int nchunks;           // coil-sum epilogue: channel chunks looped in one block
     int64_t ntiles_s;      // channel tiles per row tile (see line_grid)
     int coil_sum;
+    int pair_add;          // coil-sum epilogue with two channel chunks: both add into xout, which the
+                           // pass before cleared (two additions onto zero: the order cannot matter)
+    float2* clear;         // INV_MID: image for the next pass's pair_add, cleared here (or null)
+    int64_t nclear;
     const float2* in;
     float2* out;
     ImageSide im;

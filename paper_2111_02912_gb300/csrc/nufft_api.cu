@@ -697,13 +697,14 @@ struct Tile {
     int L1, L2, LP;   // two-phase kernel: factors and shared line pitch
 };
 
-Tile pick_tile(int L, int64_t B, int64_t S, bool coil_sum, int n_out) {
+Tile pick_tile(int L, int64_t B, int64_t S, bool coil_sum, int n_out, bool pair = false) {
     Tile t{};
     if (fft2_factor(L, t.L1, t.L2)) {
         // 8 adjacent lines (64-byte segments along the channel axis), two or three blocks per SM:
         // measured faster than 4 or 16 lines on the 640-point passes.  The coil-summing last
-        // inverse pass takes up to 16 coils per block, so 16 coils need no partial-sum pass.
-        int TL = (coil_sum && S > 8) ? 16 : 8;
+        // inverse pass takes 8 coils per block when its two coil chunks add into a cleared image
+        // (pair), else up to 16, so 16 coils need no partial-sum pass.
+        int TL = (coil_sum && S > 8 && !pair) ? 16 : 8;
         t.TS = std::min<int>(TL, pow2_ceil(S));
         t.TB = std::min<int>(TL / t.TS, pow2_ceil(B));
         t.TL = t.TB * t.TS;
@@ -894,6 +895,13 @@ int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cu
     if (!tbuf) tbuf = p->d_T;
     const float2* in = gbuf;
     ImageSide im = image_side(p, C, nullptr, smaps, xout, 0);
+    // 9..16 coils summed by two-phase passes: the last pass runs two 8-coil chunks that both add
+    // into the image, which the pass before it clears
+    bool pair = false;
+    if (smaps && D >= 2 && C > 8 && C <= 16) {
+        int l1, l2;
+        pair = fft2_factor((int)p->K[D - 1], l1, l2) && fft2_factor((int)p->K[D - 2], l1, l2);
+    }
     for (int d = 0; d < D; ++d) {
         const int L = (int)p->K[d];
         int64_t B = 1, S = C;
@@ -902,7 +910,7 @@ int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cu
         const bool last = d == D - 1;
         const bool coil_sum = last && smaps != nullptr;
         float2* out = last ? nullptr : ((d % 2 == 0) ? tbuf : gbuf);
-        Tile t = pick_tile(L, B, S, coil_sum, (int)p->N[d]);
+        Tile t = pick_tile(L, B, S, coil_sum, (int)p->N[d], pair);
         LinePass a{};
         a.ax = p->axis[d];
         a.n_in = L;
@@ -921,7 +929,14 @@ int inverse_passes(nufft_plan_s* p, int C, const float2* smaps, float2* xout, cu
         a.out = out;
         a.im = im;
         float2* part = nullptr;
-        if (coil_sum && chunks > 1) {   // partial coil sums per chunk, added in order afterwards
+        if (pair && d == D - 2) {
+            a.clear = xout;
+            a.nclear = p->Nimg;
+        }
+        if (pair && last) {
+            a.pair_add = 1;
+            a.im.xout_stride = 0;
+        } else if (coil_sum && chunks > 1) {   // partial coil sums per chunk, added in order afterwards
             part = (in == gbuf) ? tbuf : gbuf;
             a.im.xout = part;
             a.im.xout_stride = p->Nimg;

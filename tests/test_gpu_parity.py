@@ -42,7 +42,12 @@ CASES = [
     ("2d_coils_40_jvp", (16, 20), 500, 40, True, {}),        # several coil chunks in every kernel
     # grid sizes with a register-resident two-phase FFT kernel (64, 80, 96 = 8x8, 8x10, 8x12)
     ("2d_fft2_multi_image", (32, 40), 900, 3, False, {}),    # no coil sum in the last inverse pass
-    ("2d_fft2_coils_40", (32, 32), 600, 40, True, {}),       # five coil chunks of eight
+    ("2d_fft2_coils_40", (32, 32), 600, 40, True, {}),       # three coil chunks of up to sixteen
+    # 9..16 coils: the last inverse pass adds two coil chunks into the image the pass before cleared
+    ("2d_fft2_pair_c9", (32, 40), 1200, 9, True, {}),         # chunks of 8 and 1
+    ("2d_fft2_pair_c12", (40, 32), 1200, 12, True, {}),       # chunks of 8 and 4
+    ("2d_fft2_pair_c16_low_accuracy", (64, 64), 1500, 16, True, dict(J=5, sigma=1.25)),   # K = 80
+    ("3d_fft2_pair_c16", (32, 40, 48), 1500, 16, True, {}),   # cleared by the second of two middle passes
     ("2d_fft2_low_accuracy", (64, 64), 1500, 2, True, dict(J=5, sigma=1.25)),   # K = 80
     ("3d_fft2_maps", (32, 40, 48), 2000, 2, True, {}),
     ("1d_fft2", (256,), 900, 3, True, {}),
