@@ -1196,7 +1196,8 @@ int nufft_jvp_omega(nufft_plan_t p, int C, const nufft_cfloat* x, const nufft_cf
 
 // The two-stream VJP applies to 2-D strip plans with their own streams, with points, and with a
 // last inverse pass that needs no partial coil sums (16 coils or fewer with maps: one block sums
-// them all), whose buffer would be the one the omega chain uses.
+// them all, or two 8-coil blocks add into the cleared image), whose buffer would be the one the
+// omega chain uses.
 bool dual_vjp(const nufft_plan_s* p, int C, bool maps) {
     return p->aux2 && p->strip && p->D == 2 && p->M > 0 && (!maps || C <= 16);
 }
