@@ -229,6 +229,18 @@ def test_empty_and_single_point():
     y1 = plan.forward(X, S)
     torch.cuda.synchronize()
     assert rel(host(y1), jb.sense_forward(KBNufft((16, 16), one["omega"]), case["x"], case["smaps"])) < TOL_SAME
+    # no points with 16 coils on two-phase grid sizes: the last inverse pass adds two coil chunks
+    # into an image that must still come out zero (output buffers start as garbage)
+    big = make_case((32, 40), 0, 16, True, seed=5)
+    plan16 = _plan(big)
+    X16, S16 = to_dev(big["x"]), to_dev(big["smaps"])
+    out = torch.full((32, 40), float("nan"), dtype=torch.complex64, device="cuda")
+    xa16 = plan16.adjoint(to_dev(np.zeros((16, 0), np.complex64)), S16, out=out)
+    go16 = torch.empty((2, 0), dtype=torch.float32, device="cuda")
+    gx16 = torch.full((32, 40), float("nan"), dtype=torch.complex64, device="cuda")
+    plan16.vjp_omega_x(X16, to_dev(np.zeros((16, 0), np.complex64)), S16, out=(go16, gx16))
+    torch.cuda.synchronize()
+    assert float(xa16.abs().max()) == 0.0 and float(gx16.abs().max()) == 0.0 and go16.shape == (2, 0)
 
 
 def test_periodic_omega_and_boundary_values():
