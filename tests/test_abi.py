@@ -133,3 +133,51 @@ def test_table_mode_workspace_counts_the_table(abi):
     o.kernel_mode = abi.NUFFT_KERNEL_TABLE
     o.table_density = 1024
     assert abi.nufft_workspace_bytes(o, 1000, 1) == direct + (1024 * 6 // 2 + 2) * 4
+
+
+def test_largest_accepted_grids_and_first_refused(abi):
+    """Size limits, checked on the host before the device is touched: the largest 2-D grid edge
+    (K = 4096) with the most coils is accepted (its workspace is counted), one step past the edge is
+    refused, and so are 3-D grids whose first-axis channel stride would overflow the 32-bit line
+    offsets or whose bins overflow the point sort."""
+    o = abi.nufft_default_opts(2, (2048, 2048))
+    o.max_coils = abi.NUFFT_MAX_COILS
+    assert abi.nufft_workspace_bytes(o, 1000, 0) > 3 * 4096 * 4096 * abi.NUFFT_MAX_COILS * 8
+    for dim, n, coils, why in [(2, (2050, 2048), 1, "edge exceeds 4096"),
+                               (3, (1024, 1024, 1024), abi.NUFFT_MAX_COILS, "too large for max_coils"),
+                               (3, (1024, 1024, 1024), 1, "too large for the point sort")]:
+        o = abi.nufft_default_opts(dim, n)
+        o.max_coils = coils
+        assert abi.nufft_workspace_bytes(o, 1000, 0) == 0
+        with pytest.raises(abi.NufftError) as e:
+            abi.nufft_plan(o, 0, None)
+        assert e.value.status == abi.NUFFT_ERR_UNSUPPORTED and why in str(e.value)
+
+
+@pytest.mark.parametrize("field,value,status,why", [
+    ("beta", 200.0, -2, "beta too large"),
+    ("spread_variant", 9, -1, "unknown spread_variant"),
+    ("strip_part", 100, -1, "power of two"),
+    ("strip_part", 8192, -1, "power of two"),
+])
+def test_invalid_spread_and_kernel_options_are_rejected(abi, field, value, status, why):
+    o = abi.nufft_default_opts(2, (64, 64))
+    setattr(o, field, value)
+    assert abi.nufft_workspace_bytes(o, 100, 0) == 0
+    with pytest.raises(abi.NufftError) as e:
+        abi.nufft_plan(o, 0, None)
+    assert e.value.status == status and why in str(e.value)
+
+
+def test_deterministic_needs_the_strip_spread(abi):
+    o = abi.nufft_default_opts(2, (64, 64))
+    o.deterministic = 1
+    o.spread_variant = abi.NUFFT_SPREAD_STRIPS
+    assert abi.nufft_workspace_bytes(o, 100, 0) > 0
+    o.strip_part = 4096                                  # the largest part size is accepted
+    assert abi.nufft_workspace_bytes(o, 100, 0) > 0
+    o.spread_variant = abi.NUFFT_SPREAD_TILES
+    assert abi.nufft_workspace_bytes(o, 100, 0) == 0
+    with pytest.raises(abi.NufftError) as e:
+        abi.nufft_plan(o, 0, None)
+    assert e.value.status == abi.NUFFT_ERR_UNSUPPORTED and "strip spread" in str(e.value)
