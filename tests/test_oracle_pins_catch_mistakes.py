@@ -1,0 +1,108 @@
+"""The oracle's pins are sensitive: a plausible mistake planted in the oracle makes a pin fail.
+
+Each test swaps one oracle function for a copy with a typical slip (a flipped sign, an index off by
+one, a dropped or doubled factor, a transposed operand) and runs an existing pin against it, on the
+CPU; the pin must raise.  Nothing here touches the CUDA path.
+"""
+import numpy as np
+import pytest
+
+import oracle.jacobian as jacobian_mod
+import oracle.nudft as nudft_mod
+import oracle.nufft as nufft_mod
+import test_oracle_jacobian as pins_jac
+import test_oracle_nudft as pins_nudft
+import test_oracle_nufft as pins_nufft
+
+
+def _fails(pin, *args):
+    with pytest.raises(AssertionError):
+        pin(*args)
+
+
+# ---------------------------------------------------------------- exact NUDFT, Eq. (e,ndft)
+def test_flipped_exponent_sign_is_caught(monkeypatch):
+    """e^{+i omega r} in place of e^{-i omega r}: the hand closed forms and the single voxel fail."""
+    good = nudft_mod.nudft_forward
+    monkeypatch.setattr(pins_nudft, "nudft_forward", lambda x, om: good(x, -np.asarray(om)))
+    _fails(pins_nudft.test_hand_closed_forms)
+    _fails(pins_nudft.test_single_voxel)
+
+
+def test_voxel_origin_off_by_one_is_caught(monkeypatch):
+    """r = n - N/2 + 1 instead of n - N/2 (the origin of the voxel centres)."""
+    good = nudft_mod.voxel_centres
+    monkeypatch.setattr(nudft_mod, "voxel_centres", lambda shape: [r + 1 for r in good(shape)])
+    _fails(pins_nudft.test_single_voxel)
+    _fails(pins_nudft.test_hand_closed_forms)
+
+
+def test_jacobian_sign_is_caught(monkeypatch):
+    """+i r y instead of -i r y in the omega-Jacobian of the NUDFT."""
+    good = nudft_mod.nudft_jac_omega
+    monkeypatch.setattr(pins_nudft, "nudft_jac_omega", lambda x, om: -good(x, om))
+    _fails(pins_nudft.test_jacobian_matches_central_differences)
+
+
+def test_adjoint_without_conjugation_is_caught(monkeypatch):
+    """A^T y (a transposed operand, no conjugate) instead of A^H y."""
+    good = nudft_mod.nudft_adjoint
+    monkeypatch.setattr(pins_nudft, "nudft_adjoint", lambda y, om, shape: np.conj(good(np.conj(y), om, shape)))
+    _fails(pins_nudft.test_adjoint_identity)
+
+
+# ---------------------------------------------------------------- same-kernel NUFFT, Appendix
+def test_beta_typo_is_caught(monkeypatch):
+    """(sigma + 1/2) in place of (sigma - 1/2) in Beatty's formula."""
+    def bad_beta(J, sigma):
+        return np.pi * np.sqrt((J / sigma) ** 2 * (sigma + 0.5) ** 2 - 0.8)
+    monkeypatch.setattr(pins_nufft, "kb_beta", bad_beta)
+    _fails(pins_nufft.test_beta_matches_hand_evaluated_values)
+
+
+def test_dropped_scaling_is_caught(monkeypatch):
+    """The deapodisation s_n left out of the image-side scaling."""
+    monkeypatch.setattr(nufft_mod.KBNufft, "_scale_image", lambda self, x: np.asarray(x, np.complex128))
+    _fails(pins_nufft.test_nufft_close_to_exact_nudft, (16, 24), 700)
+
+
+def test_nufft_adjoint_transposed_is_caught(monkeypatch):
+    """The NUFFT adjoint computed as A~^T y instead of A~^H y."""
+    good = nufft_mod.KBNufft.adjoint
+    monkeypatch.setattr(nufft_mod.KBNufft, "adjoint", lambda self, y: np.conj(good(self, np.conj(y))))
+    _fails(pins_nufft.test_nufft_adjoint_identity)
+
+
+def test_kernel_derivative_sign_is_caught(monkeypatch):
+    """d psi / du with the wrong sign (the analytic-derivative variant of the autodiff baseline)."""
+    good = nufft_mod.kb_kernel_deriv
+    monkeypatch.setattr(pins_nufft, "kb_kernel_deriv", lambda u, J, beta: -good(u, J, beta))
+    _fails(pins_nufft.test_kernel_derivative_matches_central_differences, 6, 2.0)
+
+
+# ---------------------------------------------------------------- Jacobian products, Sec. II
+def test_vjp_gradient_factor_two_is_caught(monkeypatch):
+    """2 Re{...} with the PyTorch-convention v (the factor-2 reading of Eq. (e,jac,Ax,v))."""
+    good = jacobian_mod.vjp_omega_x
+    monkeypatch.setattr(jacobian_mod, "vjp_omega_x", lambda op, x, v, smaps=None: (2 * good(op, x, v, smaps)[0],
+                                                                                  good(op, x, v, smaps)[1]))
+    _fails(pins_jac.test_vjp_omega_matches_finite_differences)
+
+
+def test_vjp_dropped_coil_is_caught(monkeypatch):
+    """The coil sum of grad omega stopping one coil short."""
+    good = jacobian_mod.vjp_omega_x
+
+    def short(op, x, v, smaps=None):
+        v2 = np.array(v, copy=True)
+        v2[-1] = 0
+        return good(op, x, v2, smaps)[0], good(op, x, v, smaps)[1]
+    monkeypatch.setattr(jacobian_mod, "vjp_omega_x", short)
+    _fails(pins_jac.test_vjp_omega_matches_finite_differences)
+
+
+def test_jvp_sign_is_caught(monkeypatch):
+    """+i in place of -i in the JVP (the sign typo of the SENSE forward in Sec. II-G)."""
+    good = jacobian_mod.jvp_omega
+    monkeypatch.setattr(jacobian_mod, "jvp_omega", lambda op, x, dom, smaps=None: -good(op, x, dom, smaps))
+    _fails(pins_jac.test_jvp_omega_matches_finite_differences)
