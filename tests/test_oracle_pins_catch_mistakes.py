@@ -106,3 +106,72 @@ def test_jvp_sign_is_caught(monkeypatch):
     good = jacobian_mod.jvp_omega
     monkeypatch.setattr(jacobian_mod, "jvp_omega", lambda op, x, dom, smaps=None: -good(op, x, dom, smaps))
     _fails(pins_jac.test_jvp_omega_matches_finite_differences)
+
+
+# ---------------------------------------------------------------- NUFFT geometry (Appendix)
+def _retap(op, start_offset):
+    """Rebuild the interpolation windows with k = floor(t - J/2) + start_offset + (0 .. J-1)."""
+    op.taps = []
+    for d in range(op.D):
+        t = op.omega[d] * op.K[d] / (2.0 * np.pi)
+        k = (np.floor(t - op.J / 2.0) + start_offset)[:, None] + np.arange(op.J)[None, :]
+        u = t[:, None] - k
+        op.taps.append((np.mod(k.astype(np.int64), op.K[d]), nufft_mod.kb_kernel(u, op.J, op.beta), u))
+
+
+def test_window_off_by_one_is_caught(monkeypatch):
+    """The window started one cell early (the '+ 1' of k = floor(t - J/2) + 1 dropped)."""
+    good = nufft_mod.KBNufft.__init__
+
+    def bad_init(self, *args, **kw):
+        good(self, *args, **kw)
+        _retap(self, 0.0)
+    monkeypatch.setattr(nufft_mod.KBNufft, "__init__", bad_init)
+    _fails(pins_nufft.test_nufft_close_to_exact_nudft, (16, 24), 700)
+
+
+def test_image_not_wrapped_onto_the_grid_is_caught(monkeypatch):
+    """The image placed at grid indices 0 .. N-1 instead of at r mod K (no centring wrap)."""
+    good = nufft_mod.KBNufft.__init__
+
+    def bad_init(self, *args, **kw):
+        good(self, *args, **kw)
+        self.place = [np.arange(n) for n in self.shape]
+    monkeypatch.setattr(nufft_mod.KBNufft, "__init__", bad_init)
+    _fails(pins_nufft.test_nufft_close_to_exact_nudft, (16, 24), 700)
+
+
+def test_inverse_fft_in_the_forward_is_caught(monkeypatch):
+    """K * IFFT (exponent +) in place of the forward FFT of step (2)."""
+    ifftn = np.fft.ifftn
+
+    def wrong(a, axes=None):
+        n = int(np.prod([a.shape[i] for i in (axes if axes is not None else range(a.ndim))]))
+        return ifftn(a, axes=axes) * n
+    monkeypatch.setattr(nufft_mod.np.fft, "fftn", wrong)
+    _fails(pins_nufft.test_nufft_close_to_exact_nudft, (16, 24), 700)
+
+
+# ---------------------------------------------------------------- Gram and inverse Jacobians
+def test_gram_vjp_dropped_term_is_caught(monkeypatch):
+    """Eq. (e,A'A,x,omd) with its second term (+i diag{r} E' diag{E x}) left out."""
+    def first_term_only(op, x, g, smaps=None):
+        Eg = jacobian_mod.sense_forward(op, g, smaps)
+        out = np.zeros((len(op.shape), op.omega.shape[1]))
+        for d in range(len(op.shape)):
+            Exr = jacobian_mod.sense_forward(op, np.asarray(x) * jacobian_mod._r_weight(op.shape, d), smaps)
+            out[d] = np.sum(np.real(-1j * np.conj(Eg) * Exr), axis=0)
+        return out
+    monkeypatch.setattr(jacobian_mod, "gram_vjp_omega", first_term_only)
+    _fails(pins_jac.test_gram_vjp_matches_finite_differences)
+
+
+def test_psd_inverse_sign_is_caught(monkeypatch):
+    """+ in place of the - of D F^-1 b = -F^-1 (D F) F^-1 b (Eq. (e,inv,omd))."""
+    good = jacobian_mod.psd_inverse_vjp
+
+    def wrong(op, E_dense, b, g, smaps=None, lam=1e-2):
+        z, gb, go = good(op, E_dense, b, g, smaps, lam)
+        return z, gb, -go
+    monkeypatch.setattr(jacobian_mod, "psd_inverse_vjp", wrong)
+    _fails(pins_jac.test_psd_inverse_vjp_matches_finite_differences)
