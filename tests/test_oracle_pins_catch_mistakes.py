@@ -175,3 +175,17 @@ def test_psd_inverse_sign_is_caught(monkeypatch):
         return z, gb, -go
     monkeypatch.setattr(jacobian_mod, "psd_inverse_vjp", wrong)
     _fails(pins_jac.test_psd_inverse_vjp_matches_finite_differences)
+
+
+# ---------------------------------------------------------------- table autodiff (Sec. IV-A)
+def test_table_autodiff_missing_chain_factor_is_caught(monkeypatch):
+    """The autodiff slope of the table model without du / d omega = K / (2 pi)."""
+    import oracle.naive as naive_mod
+    import test_oracle_naive as pins_naive
+    good = naive_mod.TableNufft.__init__
+
+    def bad_init(self, *args, **kw):
+        good(self, *args, **kw)
+        self.dtaps = [dt * (2.0 * np.pi / self.K[d]) for d, dt in enumerate(self.dtaps)]
+    monkeypatch.setattr(naive_mod.TableNufft, "__init__", bad_init)
+    _fails(pins_naive.test_table_jacobian_is_the_derivative_of_the_piecewise_linear_model)
